@@ -1,0 +1,348 @@
+"""Benchmark of the HBGK stream-collide hot path (one JSON line on rank 0).
+
+Workload (default): D3Q19 HBGK on a 256^3 fully periodic lattice, porosity control
+from a regular matrix of equal spheres (period 32 cells, radius 0.3 of the period,
+smoothed over 2 cells), body force 1e-6 along x, tau = 0.6, FP32 deviation storage,
+two-lattice pull streaming. One benchmark step = one check interval: 100 time steps
+(fused stream-collide kernels, replayed from a CUDA graph) plus the FP64 diagnostics
+reduction (mass, momentum, plane flux, apparent permeability, residual max|du|).
+
+value : MLUPS = cells * time steps / device time (CUDA events, max over ranks).
+e2e   : the same metric through the C ABI with host buffers: per step the porosity field
+        is copied from pinned host memory (set_porosity), the lattice re-initialised,
+        100 time steps run and the diagnostics read back to the host.
+roofline : the stream-collide kernel's algorithmic bytes (q*2*sizeof(T) + 4 per cell
+        update) over its average launch time, against the measured HBM copy bandwidth.
+cpu_baseline : the FP64 CPU oracle timed on the host cores on a bounded sample (a few
+        time steps of the same 256^3 workload).
+
+--impl reference times that oracle alone (the deliberately slow reference program) on
+the same workload and prints the same line with "impl": "reference".
+Multi-GPU (torchrun): independent replicas, one lattice per GPU (weak scaling); the
+single-lattice path has no exchange step here.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 HBGK MLUPS & % HBM roofline; p50/p99 solve latency, batched vs plain"
+FALLBACK_HBM_GBS = 6800.0
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from the
+# ncu capture summarised under profiles/ (None until captured for the current kernel).
+KERNEL_TRAFFIC_BYTES = {}
+
+WORKLOADS = {
+    "d3q19_256_f32": dict(q=19, n=256, storage="f32", pattern="two", tau=0.6, F=(1e-6, 0.0, 0.0),
+                          period=32, ratio=0.3,
+                          desc="D3Q19 HBGK 256^3 periodic, regular sphere matrix (period 32, r = 0.3 P, "
+                               "smoothed), F = 1e-6, tau = 0.6, FP32 deviation storage, two-lattice"),
+    "d3q19_128_f32": dict(q=19, n=128, storage="f32", pattern="two", tau=0.6, F=(1e-6, 0.0, 0.0),
+                          period=32, ratio=0.3,
+                          desc="D3Q19 HBGK 128^3 periodic, regular sphere matrix (period 32, r = 0.3 P), FP32 "
+                               "deviation storage, two-lattice (profiling size)"),
+    "d3q19_256_f32_aa": dict(q=19, n=256, storage="f32", pattern="aa", tau=0.6, F=(1e-6, 0.0, 0.0),
+                             period=32, ratio=0.3,
+                             desc="as d3q19_256_f32 with in-place AA streaming"),
+    "d3q19_384_f16": dict(q=19, n=384, storage="f16", pattern="two", tau=0.6, F=(1e-6, 0.0, 0.0),
+                          period=32, ratio=0.3,
+                          desc="D3Q19 HBGK 384^3 periodic sphere matrix, FP16 deviation storage (s = 2^12)"),
+    "d3q19_384_bf16": dict(q=19, n=384, storage="bf16", pattern="two", tau=0.6, F=(1e-6, 0.0, 0.0),
+                           period=32, ratio=0.3,
+                           desc="D3Q19 HBGK 384^3 periodic sphere matrix, BF16 deviation storage"),
+}
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            os.unlink(self.path)
+        except Exception:
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_field(w):
+    from paper_2310_14746_gb300 import inputs
+    return inputs.regular_sphere_field(w["n"], period=w["period"], radius_ratio=w["ratio"])
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_mlups(w, varpi, steps=None, budget_s=15.0):
+    """FP64 oracle MLUPS on the full lattice of the workload; times `steps` time steps, or
+    as many as fit in ~budget_s after a 1-step probe. Returns (mlups, steps, seconds, cores)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    q, n = w["q"], w["n"]
+    f = oracle.equilibrium_state(q, (n, n, n))
+    vp = varpi.astype(np.float64)
+    if steps is None:
+        t0 = time.perf_counter()
+        f = oracle.run(f, vp, w["tau"], w["F"], (0, 0, 0), 1)
+        dt = time.perf_counter() - t0
+        steps = int(max(1, min(50, budget_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    f = oracle.run(f, vp, w["tau"], w["F"], (0, 0, 0), steps)
+    dt = time.perf_counter() - t0
+    return n ** 3 * steps / dt / 1e6, steps, dt, oracle.get_threads()
+
+
+def run_reference(args, w, rank):
+    if rank != 0:
+        return
+    varpi = make_field(w)
+    total_steps = 0
+    total_t = 0.0
+    # W warm-up + K timed oracle time steps, each a bounded sample of the workload
+    oracle_mlups(w, varpi, steps=max(1, args.warmup))
+    mlups, steps, dt, cores = oracle_mlups(w, varpi, steps=max(1, args.steps))
+    total_steps += steps
+    total_t += dt
+    value = mlups
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / total_steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["desc"], "cells": w["n"] ** 3,
+                                        "step": "one oracle time step"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": "%d FP64 oracle time steps of the full %d^3 lattice" % (steps, w["n"])},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, w, rank, world, local_rank):
+    import torch
+    import paper_2310_14746_gb300 as hb
+    from paper_2310_14746_gb300 import build
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local_rank)
+    build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    storage = {"f64": hb.HLBM_F64, "f32": hb.HLBM_F32, "f16": hb.HLBM_F16DEV, "bf16": hb.HLBM_BF16DEV}[w["storage"]]
+    pattern = hb.HLBM_AA if w["pattern"] == "aa" else hb.HLBM_TWO_LATTICE
+    n, q = w["n"], w["q"]
+    cells = n ** 3
+    inner = args.check_every
+    varpi = make_field(w)
+    varpi_pinned = torch.from_numpy(varpi).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    lat = hb.Lattice(q, n, n, n, storage, pattern)
+    lat.set_relaxation(w["tau"])
+    lat.set_force(*w["F"])
+    lat.set_porosity(varpi_pinned.numpy())
+    lat.init_equilibrium()
+
+    launches_per_step = inner + 2  # stream-collide launches + 2 reduction kernels
+
+    def one_step(ev_a=None, ev_b=None):
+        if ev_a is not None:
+            ev_a.record(stream)
+        lat.step(inner)
+        if ev_b is not None:
+            ev_b.record(stream)
+        return lat.reduce()
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        t_start.record(stream)
+        for k in range(args.steps):
+            st = one_step(*evs[k])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    kern_ms = sum(a.elapsed_time(b) for a, b in evs) / (args.steps * inner)
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = world * cells * inner * args.steps / (elapsed_ms * 1e-3) / 1e6
+
+    # ---- e2e through the C ABI with host buffers --------------------------------
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.set_porosity(varpi_pinned.numpy())  # host -> device, validated
+        lat.init_equilibrium()
+        lat.step(inner)
+        st_e2e = lat.reduce()                   # device -> host diagnostics
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * cells * inner * e2e_steps / e2e_s / 1e6
+    h2d = cells * 4 + q * 8
+    d2h = 8 * 8
+
+    bytes_per_lup = 2 * q * hb.STORAGE_BYTES[storage] + 4
+    achieved = bytes_per_lup * cells / (kern_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    kname = "stream_collide_d%dq%d_%s_%s" % (3 if q == 19 else 2, q, w["storage"], w["pattern"])
+    traffic = KERNEL_TRAFFIC_BYTES.get((kname, n))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mlups, ksteps, dt, cores = oracle_mlups(w, varpi, budget_s=args.cpu_budget)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": "%d FP64 oracle time steps of the full %d^3 lattice (%.1f s)" % (ksteps, n, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": w["storage"], "data": "synthetic",
+            "config": {"workload": w["desc"], "cells": cells, "time_steps_per_step": inner,
+                       "check_every": inner, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (%.2f GB streamed per time step)" % (bytes_per_lup * cells / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": kname, "kernel_ms": kern_ms, "bytes_per_lup": bytes_per_lup},
+            "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+            "stats": {"k_app": st["k_app"], "mass_rel_drift": st["mass"] / cells - 1.0, "max_du": st["max_du"]},
+        }
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="d3q19_256_f32")
+    ap.add_argument("--check-every", type=int, default=100)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w, rank)
+    else:
+        run_gpu(args, w, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * hlbm.h - C ABI of the GB300 homogenized lattice BGK (HBGK) library.
+ *
+ * The library advances the lattice Boltzmann discretization of the
+ * homogenized BGK Boltzmann equation (HBGKBE) of Simonis et al.,
+ * arXiv:2310.14746, Part I: BGK relaxation (Sec. 3.1, eq. collisionOperatorQ)
+ * toward the homogenized Maxwellian evaluated at the porosity-scaled velocity
+ * varpi*u (Sec. 3.2, eqs. porousVeloMaxwellian and "d definition",
+ * varpi = 1 - nu*tau/K), with a body force F (the F.grad_v f term of eq.
+ * BGKBE) and the data of the target problem eq. targetEBTL (viscosity,
+ * force, permeability via varpi, no-slip walls). The lattice pieces follow
+ * the textbook scheme, since the paper defers its discretization:
+ *   - velocity sets D2Q9 / D3Q19, lattice units dx = dt = 1, c_s^2 = 1/3,
+ *     nu = (tau - 1/2)/3;
+ *   - one time step = pull streaming g_i(x) = f_i(x - c_i) (periodic wrap, or
+ *     half-way bounce-back g_i(x) = f_opp(i)(x) across a wall), then
+ *       rho = sum g, u = (sum c g + F/2)/rho, v = varpi*u,
+ *       M_i = w_i rho (1 + 3 c_i.v + 4.5 (c_i.v)^2 - 1.5 v.v),
+ *       S_i = (1 - 1/(2 tau)) w_i (3 (c_i - u).F + 9 (c_i.u)(c_i.F)),
+ *       f_i <- g_i - (g_i - M_i)/tau + S_i;
+ *   - the state between steps is the post-collision population f.
+ *
+ * Layouts. Every cell array is x-fastest: cell = x + nx*(y + ny*z).
+ * Population arrays are [q][z][y][x]. Velocity arrays are [3][z][y][x]
+ * (component-major). Direction order:
+ *   D2Q9 : 0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1)
+ *          7 (-1,-1) 8 (1,-1)
+ *   D3Q19: 0 (0,0,0) 1 (1,0,0) 2 (-1,0,0) 3 (0,1,0) 4 (0,-1,0) 5 (0,0,1)
+ *          6 (0,0,-1) 7 (1,1,0) 8 (-1,-1,0) 9 (1,-1,0) 10 (-1,1,0)
+ *          11 (1,0,1) 12 (-1,0,-1) 13 (1,0,-1) 14 (-1,0,1) 15 (0,1,1)
+ *          16 (0,-1,-1) 17 (0,1,-1) 18 (0,-1,1)
+ * D2Q9 lattices have nz = 1.
+ *
+ * Storage. Populations are held on the device as deviations from the lattice
+ * weights, (f_i - w_i) * s, in FP64, FP32, FP16 (s = 2^12 by default) or
+ * BF16 (s = 1); arithmetic is FP32 for the reduced-precision and FP32
+ * policies and FP64 for the FP64 policy. Conversions round to nearest.
+ *
+ * Conventions shared by every call:
+ *   - the return value is a status: HLBM_OK (0) or a negative HLBM_ERR_*;
+ *     hlbm_strerror() names it. No exception crosses the ABI.
+ *   - a handle owns all device memory it allocates; inputs are copied, the
+ *     caller keeps ownership of every buffer it passes.
+ *   - device work is enqueued on the handle's CUDA stream and is asynchronous
+ *     unless the call says it synchronises.
+ *   - `on_device` = 1 means the pointer is device memory, 0 host memory.
+ *   - a handle is used by one host thread at a time.
+ */
+#ifndef HLBM_H
+#define HLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define HLBM_OK 0
+#define HLBM_ERR_INVALID_ARG (-1) /* an argument is out of range or NULL     */
+#define HLBM_ERR_OOM (-2)         /* a device or host allocation failed      */
+#define HLBM_ERR_CUDA (-3)        /* a CUDA runtime call or launch failed    */
+#define HLBM_ERR_NOT_CONVERGED (-4)
+#define HLBM_ERR_TIMEOUT (-5)
+#define HLBM_ERR_BUSY (-6)
+#define HLBM_ERR_IO (-7)          /* file open/read/write failed or bad file */
+#define HLBM_ERR_STATE (-8)       /* the call needs a setting not yet made   */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define HLBM_D2Q9 9
+#define HLBM_D3Q19 19
+
+#define HLBM_F64 0
+#define HLBM_F32 1
+#define HLBM_F16DEV 2
+#define HLBM_BF16DEV 3
+
+#define HLBM_TWO_LATTICE 0 /* pull from buffer A into buffer B, swap        */
+#define HLBM_AA 1          /* in place, alternating local / neighbour steps */
+
+#define HLBM_PERIODIC 0
+#define HLBM_HALFWAY_BOUNCE_BACK 1 /* walls half a cell outside both ends  */
+
+typedef struct hlbm_lattice hlbm_t;
+
+/* FP64 diagnostics of the current state (see hlbm_reduce). */
+typedef struct {
+    double mass;        /* sum over cells of rho                            */
+    double momentum[3]; /* sum over cells of rho*u                          */
+    double plane_flux;  /* sum over the plane x = nx-1 of rho*u_x           */
+    double k_app;       /* nu * mean(rho*u_x) / F_x (0 if F_x == 0)         */
+    double max_du;      /* max over cells, components of |u - u_prev|       */
+    double max_u;       /* max over cells, components of |u|                */
+    long long step;     /* time steps taken since the last initialisation   */
+} hlbm_stats;
+
+/* ---- lattice lifetime -------------------------------------------------- */
+
+/* Create a lattice of nx*ny*nz cells with velocity set `velset`
+ * (HLBM_D2Q9 needs nz == 1), storage policy `storage` and streaming
+ * pattern `pattern`; work goes on `cuda_stream` (a cudaStream_t; NULL is the
+ * legacy default stream) of the current device. Defaults: tau = 1, F = 0,
+ * all axes periodic, varpi = 1 everywhere, populations at rest (f = w).
+ * On error *out is NULL. Cites: the lattice and its data are the problem
+ * statement of eq. targetEBTL and of the HBGKBE (Sec. 3.2). */
+int hlbm_create(hlbm_t** out, int velset, int nx, int ny, int nz, int storage, int pattern,
+                void* cuda_stream);
+
+/* Free the handle and its device memory (after draining its stream). NULL is a no-op. */
+void hlbm_destroy(hlbm_t* h);
+
+/* Replace the stream later work is enqueued on. */
+int hlbm_set_stream(hlbm_t* h, void* cuda_stream);
+
+/* ---- problem data ------------------------------------------------------ */
+
+/* BGK relaxation time tau (eq. collisionOperatorQ); viscosity nu = (tau - 1/2)/3.
+ * Rejects tau <= 1/2 and non-finite values. */
+int hlbm_set_relaxation(hlbm_t* h, double tau);
+
+/* Per-cell porosity control varpi (eq. "d definition"), nx*ny*nz FP32 values,
+ * x-fastest; copied. Every value must lie in [0, 1] (NaN rejected); a host
+ * array is validated before the copy, a device array by a check kernel
+ * (synchronises). varpi = 1 is plain BGK, varpi = 0 a solid cell. */
+int hlbm_set_porosity(hlbm_t* h, const float* varpi, int on_device);
+
+/* varpi = 1 - nu*tau/K for n host values (eq. "d definition"), clamped to
+ * [0, 1]; K <= 0 or NaN gives 0, K = +inf gives 1. Pure host function. */
+int hlbm_porosity_from_permeability(const float* K, double nu, double tau, float* varpi,
+                                    size_t n);
+
+/* Constant body force (lattice units) F of eq. targetEBTL; D2Q9 ignores Fz. */
+int hlbm_set_force(hlbm_t* h, double Fx, double Fy, double Fz);
+
+/* Boundary type of axis 0 (x), 1 (y) or 2 (z): HLBM_PERIODIC or
+ * HLBM_HALFWAY_BOUNCE_BACK (no-slip u = 0 on the boundary, eq. targetEBTL). */
+int hlbm_set_boundary(hlbm_t* h, int axis, int type);
+
+/* Storage scale s of the FP16 deviation policy (a power of two in
+ * [1, 2^20]); other policies accept only 1. Applies to later writes of
+ * the state: call before hlbm_init_equilibrium / hlbm_set_populations. */
+int hlbm_set_storage_scale(hlbm_t* h, double s);
+
+/* Set every cell to the equilibrium of (rho0, u0) (unscaled by varpi) and
+ * reset the step counter and the residual reference velocity (to 0). */
+int hlbm_init_equilibrium(hlbm_t* h, double rho0, double ux, double uy, double uz);
+
+/* Set the post-collision state from q*cells FP64 full populations f
+ * ([q][z][y][x]); resets the step counter and the residual reference. */
+int hlbm_set_populations(hlbm_t* h, const double* f, int on_device);
+
+/* Read the post-collision state as q*cells FP64 full populations.
+ * A host destination synchronises. */
+int hlbm_get_populations(hlbm_t* h, double* f, int on_device);
+
+/* ---- time stepping ----------------------------------------------------- */
+
+/* Advance nsteps >= 0 time steps (stream + collide, see above). Asynchronous.
+ * Runs of at least 8 steps replay a captured CUDA graph of the step
+ * sequence; shorter runs launch directly. */
+int hlbm_step(hlbm_t* h, long nsteps);
+
+/* Steps taken since the last initialisation. */
+int hlbm_get_step(hlbm_t* h, long long* step);
+
+/* ---- observables ------------------------------------------------------- */
+
+/* Density rho (cells values) and velocity u ([3][cells]) of the current
+ * state: the moments of Def. moments of the streamed populations, with the
+ * half-force velocity u = (sum c g + F/2)/rho. Either pointer may be NULL.
+ * FP32 outputs. A host destination synchronises. */
+int hlbm_moments(hlbm_t* h, float* rho, float* u, int on_device);
+
+/* As hlbm_moments with FP64 outputs (for FP64-storage parity checks). */
+int hlbm_moments_f64(hlbm_t* h, double* rho, double* u, int on_device);
+
+/* FP64 diagnostics of the current state (struct hlbm_stats): totals in a
+ * fixed-order (deterministic) reduction tree, the apparent permeability of
+ * Darcy's law (Thm. thmStatNSECase4, u = A(F - grad p)/nu, mean over all
+ * cells), and the residual max|u - u_prev| against the velocity seen by the
+ * previous hlbm_reduce call (or 0 after initialisation), which this call then
+ * replaces. Synchronises. */
+int hlbm_reduce(hlbm_t* h, hlbm_stats* out);
+
+/* ---- checkpoint -------------------------------------------------------- */
+
+/* Write the state, step counter and parameters to a file / read them back
+ * into a handle of the same shape, velocity set and storage. Both
+ * synchronise. Resuming gives the same bits as an uninterrupted run. */
+int hlbm_save(hlbm_t* h, const char* path);
+int hlbm_load(hlbm_t* h, const char* path);
+
+/* ---- misc -------------------------------------------------------------- */
+
+/* Static description of a status code. */
+const char* hlbm_strerror(int status);
+
+/* Last CUDA error string recorded by the library on this thread ("" if none). */
+const char* hlbm_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HLBM_H */

@@ -1,0 +1,59 @@
+// Internal interface between the C ABI (api.cu) and the kernel translation
+// units. Not installed; callers use include/hlbm.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace hlbm {
+
+enum StepMode { MODE_TWO_LATTICE = 0, MODE_AA_EVEN = 1, MODE_AA_ODD = 2 };
+
+// Everything a launch needs to know about a lattice, in plain types.
+struct LaunchCtx {
+    int q;          // 9 or 19
+    int storage;    // HLBM_F64 / F32 / F16DEV / BF16DEV
+    int nx, ny, nz;
+    int wall[3];    // 1 = half-way bounce-back on that axis
+    double tau;
+    double F[3];
+    double scale;   // storage scale s (deviations are stored times s)
+    cudaStream_t stream;
+};
+
+// One time step: read `fin` in the layout implied by `mode`, write `fout`
+// (== fin for the AA modes).
+cudaError_t launch_step(const LaunchCtx& c, int mode, const void* fin, void* fout,
+                        const float* varpi);
+
+// Moments of a state stored in `layout` (Layout enum of lattice.cuh). rho
+// and/or u may be null. out_f64 selects double outputs, else float.
+cudaError_t launch_moments(const LaunchCtx& c, int layout, const void* f, void* rho, void* u,
+                           int out_f64);
+
+// Per-block FP64 partials of the diagnostics, then a single-block fixed-order
+// final reduction into out8[8] (device). u_prev (arithmetic type of the
+// storage: double for F64, float otherwise; 3*cells) is compared against and,
+// if update_prev, overwritten. `partials` is caller-provided scratch of at
+// least reduce_partials_count(c) * 8 doubles.
+size_t reduce_partials_count(const LaunchCtx& c);
+cudaError_t launch_reduce(const LaunchCtx& c, int layout, const void* f, void* u_prev,
+                          int update_prev, double* partials, double* out8);
+
+// Write the natural post-collision populations fnat (FP64 full values) into
+// the state buffer in `layout`. fnat is [q][cells] when uniform == 0, or q
+// values applied to every cell when uniform == 1.
+cudaError_t launch_write_state(const LaunchCtx& c, int layout, const double* fnat, int uniform,
+                               void* f);
+// Read the state as natural FP64 full populations [q][cells].
+cudaError_t launch_read_state(const LaunchCtx& c, int layout, const void* f, double* fnat);
+
+// Count values outside [0, 1] (or NaN) into *bad (device int, accumulated).
+cudaError_t launch_check_unit_interval(const float* v, size_t n, int* bad, cudaStream_t s);
+cudaError_t launch_fill_f32(float* v, size_t n, float value, cudaStream_t s);
+cudaError_t launch_fill_bytes0(void* p, size_t bytes, cudaStream_t s);
+
+size_t storage_bytes(int storage);
+
+}  // namespace hlbm

@@ -1,0 +1,97 @@
+// Fused HBGK stream-and-collide kernels (one time step over every cell).
+//
+// One thread per cell; threads run along x so that each of the q population
+// planes is read and written by whole warps over contiguous x (the +-1 x
+// shifts of the pull make those loads straddle a sector boundary, which the
+// L1/L2 absorb). Per cell: q loads, moments, the homogenized equilibrium at
+// varpi*u (Sec. 3.2, eq. porousVeloMaxwellian), Guo forcing, BGK relaxation
+// (eq. collisionOperatorQ), q stores. Bytes per cell update: 2*q*sizeof(T)
+// for the populations plus 4 for varpi.
+#include "internal.h"
+#include "lattice.cuh"
+
+namespace hlbm {
+
+template <int Q, class S, bool WALLS, int MODE>
+__global__ void __launch_bounds__(256)
+k_step(const typename S::T* fin, typename S::T* fout, const float* __restrict__ varpi,
+       Geometry g, Phys<typename S::C> ph, typename S::C s, typename S::C inv_s) {
+    using C = typename S::C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const Nbr nb(g, x, y, z);
+    const size_t cell = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * (size_t)z);
+    constexpr int lay_in = MODE == MODE_TWO_LATTICE ? NATURAL : (MODE == MODE_AA_EVEN ? STREAMED : SWAPPED);
+    constexpr int lay_out = MODE == MODE_TWO_LATTICE ? NATURAL : (MODE == MODE_AA_EVEN ? SWAPPED : STREAMED);
+
+    C d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = S::load(fin, gather_index<Q, WALLS>(g, nb, cell, i, lay_in), inv_s);
+
+    collide<Q, C>(d, C(__ldg(varpi + cell)), ph);
+
+#pragma unroll
+    for (int i = 0; i < Q; ++i) S::store(fout, natural_index<Q, WALLS>(g, nb, cell, i, lay_out), d[i], s);
+}
+
+static dim3 block_for(int nx) {
+    int bx = ((nx + 31) / 32) * 32;
+    if (bx > 128) bx = 128;
+    return dim3(bx, 256 / bx, 1);
+}
+
+template <int Q, class S, bool WALLS>
+static cudaError_t step_impl(const LaunchCtx& c, int mode, const void* fin, void* fout,
+                             const float* varpi) {
+    using C = typename S::C;
+    using T = typename S::T;
+    Geometry g{c.nx, c.ny, c.nz, c.wall[0], c.wall[1], c.wall[2], (size_t)c.nx * c.ny * c.nz};
+    Phys<C> ph{C(1.0 / c.tau), C(1.0 - 0.5 / c.tau), C(c.F[0]), C(c.F[1]), Q == 9 ? C(0) : C(c.F[2])};
+    const dim3 blk = block_for(c.nx);
+    const dim3 grd((c.nx + blk.x - 1) / blk.x, (c.ny + blk.y - 1) / blk.y, c.nz);
+    const C s = C(c.scale), inv_s = C(1.0 / c.scale);
+    const T* a = static_cast<const T*>(fin);
+    T* b = static_cast<T*>(fout);
+    switch (mode) {
+        case MODE_TWO_LATTICE:
+            k_step<Q, S, WALLS, MODE_TWO_LATTICE><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s);
+            break;
+        case MODE_AA_EVEN:
+            k_step<Q, S, WALLS, MODE_AA_EVEN><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s);
+            break;
+        case MODE_AA_ODD:
+            k_step<Q, S, WALLS, MODE_AA_ODD><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int Q, class S>
+static cudaError_t step_w(const LaunchCtx& c, int mode, const void* fin, void* fout, const float* varpi) {
+    const bool walls = c.wall[0] || c.wall[1] || c.wall[2];
+    return walls ? step_impl<Q, S, true>(c, mode, fin, fout, varpi)
+                 : step_impl<Q, S, false>(c, mode, fin, fout, varpi);
+}
+
+template <int Q>
+static cudaError_t step_s(const LaunchCtx& c, int mode, const void* fin, void* fout, const float* varpi) {
+    switch (c.storage) {
+        case 0: return step_w<Q, StoreF64>(c, mode, fin, fout, varpi);
+        case 1: return step_w<Q, StoreF32>(c, mode, fin, fout, varpi);
+        case 2: return step_w<Q, StoreF16>(c, mode, fin, fout, varpi);
+        case 3: return step_w<Q, StoreBF16>(c, mode, fin, fout, varpi);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step(const LaunchCtx& c, int mode, const void* fin, void* fout, const float* varpi) {
+    if (c.q == 9) return step_s<9>(c, mode, fin, fout, varpi);
+    if (c.q == 19) return step_s<19>(c, mode, fin, fout, varpi);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace hlbm
