@@ -183,6 +183,23 @@ int hlbm_moments_f64(hlbm_t* h, double* rho, double* u, int on_device);
  * replaces. Synchronises. */
 int hlbm_reduce(hlbm_t* h, hlbm_stats* out);
 
+/* ---- differentiation ---------------------------------------------------- */
+
+/* Gradient of the outflow mass flux through the plane x = plane_x,
+ *   J = sum_{y,z} rho*u_x  (the moments of Def. moments, half-force velocity),
+ * evaluated nsteps time steps after the current state, with respect to the
+ * per-cell porosity control varpi (eq. "d definition"), by a hand-written
+ * discrete adjoint of the step: the forward run keeps the state every
+ * ckpt_every steps, and each segment is recomputed before its reverse steps
+ * (memory: about (nsteps/ckpt_every + ckpt_every + 2) lattice states, plus
+ * two FP32 adjoint fields, allocated for the call and freed after it).
+ * Writes J (one host double) and grad_varpi (cells FP32 values, x-fastest,
+ * host or device per on_device). The lattice state afterwards is the forward
+ * state after nsteps steps, and the step counter advances by nsteps.
+ * Synchronises. Rejects nsteps < 0, ckpt_every < 1, plane_x outside [0, nx). */
+int hlbm_adjoint_flux_grad(hlbm_t* h, long nsteps, int ckpt_every, int plane_x, double* J,
+                           float* grad_varpi, int on_device);
+
 /* ---- checkpoint -------------------------------------------------------- */
 
 /* Write the state, step counter and parameters to a file / read them back

@@ -424,8 +424,10 @@ static void or_stream_transpose(const or_velset* vs, const int n[3], const int b
                                 const double* mu, double* out)
 {
     int64_t cells = (int64_t)n[0] * n[1] * n[2];
-    int x, y, z, i, d;
-    for (z = 0; z < n[2]; ++z)
+    int z;
+#pragma omp parallel for schedule(static)
+    for (z = 0; z < n[2]; ++z) {
+        int x, y, i, d;
         for (y = 0; y < n[1]; ++y)
             for (x = 0; x < n[0]; ++x)
                 for (i = 0; i < vs->q; ++i) {
@@ -444,6 +446,7 @@ static void or_stream_transpose(const or_velset* vs, const int n[3], const int b
                         out[(int64_t)i * cells + cell] =
                             mu[(int64_t)i * cells + s[0] + (int64_t)n[0] * (s[1] + (int64_t)n[1] * s[2])];
                 }
+    }
 }
 
 /* One reverse step: given the forward state f^n (post-collision, before the
@@ -460,6 +463,7 @@ int oracle_adjoint_step(int q, int nx, int ny, int nz, const int* bc, double tau
     if (or_get_velset(q, &vs)) return -1;
     mu = (double*)malloc(sizeof(double) * (size_t)(q * cells));
     if (!mu) return -2;
+#pragma omp parallel for private(x, y, i) schedule(static)
     for (z = 0; z < nz; ++z)
         for (y = 0; y < ny; ++y)
             for (x = 0; x < nx; ++x) {

@@ -95,6 +95,7 @@ SIGNATURES = {
     "hlbm_moments": (_i, [_vp, _vp, _vp, _i]),
     "hlbm_moments_f64": (_i, [_vp, _vp, _vp, _i]),
     "hlbm_reduce": (_i, [_vp, ctypes.POINTER(hlbm_stats)]),
+    "hlbm_adjoint_flux_grad": (_i, [_vp, ctypes.c_long, _i, _i, ctypes.POINTER(_d), _vp, _i]),
     "hlbm_save": (_i, [_vp, ctypes.c_char_p]),
     "hlbm_load": (_i, [_vp, ctypes.c_char_p]),
     "hlbm_strerror": (ctypes.c_char_p, [_i]),
@@ -264,6 +265,15 @@ def hlbm_reduce(h):
     return st.as_dict()
 
 
+def hlbm_adjoint_flux_grad(h, nsteps, ckpt_every, plane_x, grad):
+    """Returns J; writes dJ/dvarpi into grad (float32 numpy array or CUDA tensor)."""
+    p, dev = _ptr(grad, np.float32)
+    J = _d(0.0)
+    _check(_lib().hlbm_adjoint_flux_grad(h, int(nsteps), int(ckpt_every), int(plane_x), ctypes.byref(J), p, dev),
+           "hlbm_adjoint_flux_grad")
+    return J.value
+
+
 def hlbm_save(h, path):
     _check(_lib().hlbm_save(h, os.fsencode(path)), "hlbm_save")
 
@@ -357,6 +367,14 @@ class Lattice:
 
     def reduce(self):
         return hlbm_reduce(self.h)
+
+    def adjoint_flux_grad(self, nsteps, ckpt_every=45, plane_x=None, grad=None):
+        """(J, dJ/dvarpi) of the outflow flux through x = plane_x (default nx-1) after nsteps."""
+        if grad is None:
+            grad = np.empty(self.shape, dtype=np.float32)
+        px = self.nx - 1 if plane_x is None else plane_x
+        J = hlbm_adjoint_flux_grad(self.h, nsteps, ckpt_every, px, grad)
+        return J, grad
 
     def save(self, path):
         hlbm_save(self.h, path)

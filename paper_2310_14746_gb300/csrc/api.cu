@@ -497,6 +497,110 @@ int hlbm_reduce(hlbm_t* h, hlbm_stats* out) {
     return HLBM_OK;
 }
 
+namespace {
+
+// Device allocations of one call, released on every exit path (stream-ordered).
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch() {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+    }
+    cudaError_t alloc(void** p, size_t bytes) {
+        cudaError_t e = cudaMallocAsync(p, bytes, s);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+};
+
+// Copy the current state into `dst` in the NATURAL layout.
+int copy_natural(hlbm_t* h, void* dst, Scratch& sc) {
+    if (h->pattern == HLBM_TWO_LATTICE) {
+        HLBM_CUDA(cudaMemcpyAsync(dst, h->state(), h->state_bytes(), cudaMemcpyDeviceToDevice, h->stream));
+        return HLBM_OK;
+    }
+    double* tmp = nullptr;
+    HLBM_CUDA(sc.alloc((void**)&tmp, (size_t)h->q * h->cells * sizeof(double)));
+    HLBM_CUDA(launch_read_state(h->ctx(h->stream), h->layout(), h->state(), tmp));
+    HLBM_CUDA(launch_write_state(h->ctx(h->stream), kNatural, tmp, 0, dst));
+    return HLBM_OK;
+}
+
+// Make a NATURAL-layout buffer the handle's state.
+int adopt_natural(hlbm_t* h, const void* src, Scratch& sc) {
+    if (h->pattern == HLBM_TWO_LATTICE) {
+        HLBM_CUDA(cudaMemcpyAsync(h->buf[0], src, h->state_bytes(), cudaMemcpyDeviceToDevice, h->stream));
+        h->cur = 0;
+        return HLBM_OK;
+    }
+    double* tmp = nullptr;
+    HLBM_CUDA(sc.alloc((void**)&tmp, (size_t)h->q * h->cells * sizeof(double)));
+    HLBM_CUDA(launch_read_state(h->ctx(h->stream), kNatural, src, tmp));
+    h->aa_odd = 0;
+    HLBM_CUDA(launch_write_state(h->ctx(h->stream), h->layout(), tmp, 0, h->buf[0]));
+    return HLBM_OK;
+}
+
+}  // namespace
+
+int hlbm_adjoint_flux_grad(hlbm_t* h, long nsteps, int every, int plane_x, double* J, float* grad, int on_device) {
+    if (!h || !J || !grad || nsteps < 0 || every < 1 || plane_x < 0 || plane_x >= (h ? h->nx : 0))
+        return HLBM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    const size_t sb = h->state_bytes();
+    const size_t N = h->cells;
+    const long nsnap = nsteps > 0 ? (nsteps - 1) / every + 1 : 1;
+    const int nseg = every > 2 ? every : 2;  // slot 0/1 double as forward ping-pong buffers
+    const LaunchCtx c = h->ctx(h->stream);
+    Scratch sc(h->stream);
+    char *snaps = nullptr, *seg = nullptr;
+    float *lam_a = nullptr, *lam_b = nullptr, *gacc = nullptr;
+    double* jdev = nullptr;
+    HLBM_CUDA(sc.alloc((void**)&snaps, sb * nsnap));
+    HLBM_CUDA(sc.alloc((void**)&seg, sb * nseg));
+    HLBM_CUDA(sc.alloc((void**)&lam_a, (size_t)h->q * N * sizeof(float)));
+    HLBM_CUDA(sc.alloc((void**)&lam_b, (size_t)h->q * N * sizeof(float)));
+    HLBM_CUDA(sc.alloc((void**)&gacc, N * sizeof(float)));
+    HLBM_CUDA(sc.alloc((void**)&jdev, sizeof(double)));
+    int rc = copy_natural(h, snaps, sc);
+    if (rc != HLBM_OK) return rc;
+
+    // forward sweep, keeping f^{k*every}
+    void* a = snaps;
+    for (long s = 0; s < nsteps; ++s) {
+        const bool keep = (s + 1) % every == 0 && (s + 1) / every < nsnap;
+        void* b = keep ? (void*)(snaps + sb * ((s + 1) / every)) : (void*)(seg + sb * ((s + 1) & 1));
+        HLBM_CUDA(launch_step(c, MODE_TWO_LATTICE, a, b, h->varpi));
+        a = b;
+    }
+    HLBM_CUDA(launch_plane_flux(c, kNatural, a, plane_x, jdev));
+    rc = adopt_natural(h, a, sc);
+    if (rc != HLBM_OK) return rc;
+
+    // reverse sweep
+    HLBM_CUDA(launch_flux_seed(c, lam_a, plane_x));
+    HLBM_CUDA(cudaMemsetAsync(gacc, 0, N * sizeof(float), h->stream));
+    for (long sg = nsnap - 1; sg >= 0 && nsteps > 0; --sg) {
+        const long s0 = sg * every;
+        const long s1 = s0 + every < nsteps ? s0 + every : nsteps;
+        auto state = [&](long k) -> void* { return k == 0 ? (void*)(snaps + sb * sg) : (void*)(seg + sb * k); };
+        for (long k = 0; k + 1 < s1 - s0; ++k) HLBM_CUDA(launch_step(c, MODE_TWO_LATTICE, state(k), state(k + 1), h->varpi));
+        for (long s = s1 - 1; s >= s0; --s) {
+            HLBM_CUDA(launch_adjoint_step(c, state(s - s0), lam_a, lam_b, h->varpi, gacc));
+            float* t = lam_a;
+            lam_a = lam_b;
+            lam_b = t;
+        }
+    }
+    HLBM_CUDA(cudaMemcpyAsync(grad, gacc, N * sizeof(float),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    HLBM_CUDA(cudaMemcpyAsync(J, jdev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    HLBM_CUDA(cudaStreamSynchronize(h->stream));
+    h->step += nsteps;
+    return HLBM_OK;
+}
+
 int hlbm_save(hlbm_t* h, const char* path) {
     if (!h || !path) return HLBM_ERR_INVALID_ARG;
     DeviceGuard g(h->device);

@@ -56,4 +56,14 @@ cudaError_t launch_fill_bytes0(void* p, size_t bytes, cudaStream_t s);
 
 size_t storage_bytes(int storage);
 
+// Reverse step of the outflow-flux adjoint: fn is the forward state before the
+// step (NATURAL layout), lam_in = dJ/df^{n+1} and lam_out = dJ/df^n ([q][cells]
+// FP32, distinct buffers); grad (FP32 cells) accumulates dJ/dvarpi.
+cudaError_t launch_adjoint_step(const LaunchCtx& c, const void* fn, const float* lam_in, float* lam_out,
+                                const float* varpi, float* grad);
+// dJ/df of the final state for J = sum over the plane x = plane_x of rho*u_x.
+cudaError_t launch_flux_seed(const LaunchCtx& c, float* lam, int plane_x);
+// J of a state in `layout` into out (one double, device).
+cudaError_t launch_plane_flux(const LaunchCtx& c, int layout, const void* f, int plane_x, double* out);
+
 }  // namespace hlbm

@@ -1,0 +1,223 @@
+// Discrete adjoint of the HBGK step, for the gradient of the outflow flux
+// J = sum_{y,z} rho*u_x over a plane x = plane_x of the final state with
+// respect to the per-cell porosity control varpi (eq. "d definition").
+//
+// Forward step: f^{n+1} = C(S f^n; varpi) with S the pull streaming and C the
+// per-cell HBGK collision. Reverse step, with lam = dJ/df^{n+1}:
+//   mu(x)    = (dC/dg)^T lam(x)   at g = (S f^n)(x)
+//   grad(x) += (dC/dvarpi(x))^T lam(x)
+//   dJ/df^n  = S^T mu,  (S^T mu)_k(y) = mu_k(y + c_k), or mu_opp(k)(y) when
+//              y + c_k lies beyond a wall.
+// (dC/dg)^T lam = (1 - 1/tau) lam + a_rho + c . a_j is the diagonal plus a
+// rank-4 correction through the moments (rho, j); the kernel evaluates it
+// per cell and pushes mu to its transposed-streaming destinations. Bytes per
+// cell update: q loads of the forward state, q loads and q stores of the
+// adjoint (FP32), varpi, and the gradient read-modify-write.
+#include "internal.h"
+#include "lattice.cuh"
+
+namespace hlbm {
+
+static dim3 block_for(int nx) {
+    int bx = ((nx + 31) / 32) * 32;
+    if (bx > 128) bx = 128;
+    return dim3(bx, 256 / bx, 1);
+}
+
+static Geometry geom(const LaunchCtx& c) {
+    return Geometry{c.nx, c.ny, c.nz, c.wall[0], c.wall[1], c.wall[2], (size_t)c.nx * c.ny * c.nz};
+}
+
+template <int Q, class S, bool WALLS>
+__global__ void __launch_bounds__(256)
+k_adjoint_step(const typename S::T* __restrict__ fn, const float* __restrict__ lam_in, float* __restrict__ lam_out,
+               const float* __restrict__ varpi, float* __restrict__ grad, Geometry g, Phys<typename S::C> ph,
+               typename S::C inv_s) {
+    using C = typename S::C;
+    using L = Lat<Q>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const Nbr nb(g, x, y, z);
+    const size_t cell = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * (size_t)z);
+    const size_t N = g.N;
+
+    // forward quantities at g = S f^n
+    C d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = S::load(fn, gather_index<Q, WALLS>(g, nb, cell, i, NATURAL), inv_s);
+    C drho, mx, my, mz;
+    moments<Q, C>(d, ph, drho, mx, my, mz);
+    const C rho = C(1) + drho;
+    const C inv_rho = C(1) / rho;
+    const C ux = mx * inv_rho, uy = my * inv_rho, uz = mz * inv_rho;
+    const C vp = C(__ldg(varpi + cell));
+    const C vx = vp * ux, vy = vp * uy, vz = vp * uz;
+    const C vv = vx * vx + vy * vy + vz * vz;
+    const C omega = ph.omega;
+
+    // accumulate b_u = sum lam_i d(M_i/tau + S_i)/du, b_rho = sum lam_i w_i P_i / tau,
+    // and dvarpi = sum lam_i w_i rho (dP/dv . u) / tau
+    C lam[Q];
+    C bux = 0, buy = 0, buz = 0, brho = 0, dvp = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        lam[i] = __ldg(lam_in + (size_t)i * N + cell);
+        const C cx = C(L::cx(i)), cy = C(L::cy(i)), cz = C(L::cz(i));
+        const C w = C(L::w(i));
+        const C cv = cx * vx + cy * vy + cz * vz;
+        const C cF = cx * ph.Fx + cy * ph.Fy + cz * ph.Fz;
+        const C P = C(1) + C(3) * cv + C(4.5) * cv * cv - C(1.5) * vv;
+        // dP/dv = 3 c + 9 (c.v) c - 3 v
+        const C dPx = C(3) * cx + C(9) * cv * cx - C(3) * vx;
+        const C dPy = C(3) * cy + C(9) * cv * cy - C(3) * vy;
+        const C dPz = C(3) * cz + C(9) * cv * cz - C(3) * vz;
+        const C lw = lam[i] * w;
+        const C a = lw * rho * vp * omega;      // d(M_i/tau)/du = w rho varpi dP/dv / tau
+        const C b = lw * ph.guo;                // dS_i/du = guo w (-3 F + 9 (c.F) c)
+        bux += a * dPx + b * (C(-3) * ph.Fx + C(9) * cF * cx);
+        buy += a * dPy + b * (C(-3) * ph.Fy + C(9) * cF * cy);
+        buz += a * dPz + b * (C(-3) * ph.Fz + C(9) * cF * cz);
+        brho += lw * P * omega;
+        dvp += lw * rho * omega * (dPx * ux + dPy * uy + dPz * uz);
+    }
+    // u = (j + F/2)/rho: du/dj = I/rho, du/drho = -u/rho
+    const C a_rho = brho - (bux * ux + buy * uy + buz * uz) * inv_rho;
+    const C ajx = bux * inv_rho, ajy = buy * inv_rho, ajz = buz * inv_rho;
+    grad[cell] += float(dvp);
+
+    const C keep = C(1) - omega;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const C mu = keep * lam[k] + a_rho + C(L::cx(k)) * ajx + C(L::cy(k)) * ajy + C(L::cz(k)) * ajz;
+        // (S^T mu)_k(y) = mu_k(y + c_k): mu_k(x) goes to y = x - c_k, or, when x - c_k
+        // lies beyond a wall, to slot opp(k) of x itself.
+        const bool wall = WALLS && nb.beyond_wall<Q>(k, -1);
+        const size_t dst = wall ? (size_t)opp<Q>(k) * N + cell : (size_t)k * N + nb.cell_at<Q>(g, k, -1);
+        lam_out[dst] = float(mu);
+    }
+}
+
+// Seed dJ/df^N = S^T e, e_k(x) = c_kx on the plane x = plane_x (rho*u_x of the
+// streamed populations is sum_k c_kx g_k + F_x/2).
+template <int Q, bool WALLS>
+__global__ void __launch_bounds__(256) k_flux_seed(float* lam, Geometry g, int plane_x) {
+    using L = Lat<Q>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const Nbr nb(g, x, y, z);
+    const size_t cell = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * (size_t)z);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        // (S^T e)_k(y) = e_k(y + c_k), or e_opp(k)(y) across a wall
+        float v;
+        if (WALLS && nb.beyond_wall<Q>(k, +1)) {
+            v = (x == plane_x) ? float(L::cx(opp<Q>(k))) : 0.0f;
+        } else {
+            const int dx = L::cx(k);
+            const int xs = dx > 0 ? nb.xp : (dx < 0 ? nb.xm : x);
+            v = (xs == plane_x) ? float(dx) : 0.0f;
+        }
+        lam[(size_t)k * g.N + cell] = v;
+    }
+}
+
+// J = sum over the plane x = plane_x of rho*u_x = (j_x + F_x/2), FP64, one block,
+// fixed order.
+template <int Q, class S, bool WALLS>
+__global__ void __launch_bounds__(256)
+k_plane_flux(const typename S::T* f, int lay, Geometry g, Phys<typename S::C> ph, typename S::C inv_s,
+             int plane_x, double* out) {
+    using C = typename S::C;
+    __shared__ double sh[256];
+    double acc = 0.0;
+    const int rows = g.ny * g.nz;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const int y = r % g.ny, z = r / g.ny;
+        const Nbr nb(g, plane_x, y, z);
+        const size_t cell = (size_t)plane_x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * (size_t)z);
+        C d[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = S::load(f, gather_index<Q, WALLS>(g, nb, cell, i, lay), inv_s);
+        C drho, mx, my, mz;
+        moments<Q, C>(d, ph, drho, mx, my, mz);
+        acc += (double)mx;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+template <int Q, class S, bool WALLS>
+static cudaError_t adjoint_impl(const LaunchCtx& c, const void* fn, const float* lam_in, float* lam_out,
+                                const float* varpi, float* grad) {
+    using C = typename S::C;
+    const Geometry g = geom(c);
+    Phys<C> ph{C(1.0 / c.tau), C(1.0 - 0.5 / c.tau), C(c.F[0]), C(c.F[1]), Q == 9 ? C(0) : C(c.F[2])};
+    const dim3 blk = block_for(c.nx);
+    const dim3 grd((c.nx + blk.x - 1) / blk.x, (c.ny + blk.y - 1) / blk.y, c.nz);
+    k_adjoint_step<Q, S, WALLS><<<grd, blk, 0, c.stream>>>(static_cast<const typename S::T*>(fn), lam_in, lam_out,
+                                                           varpi, grad, g, ph, C(1.0 / c.scale));
+    return cudaGetLastError();
+}
+
+template <int Q, class S, class Fn>
+static cudaError_t with_walls(const LaunchCtx& c, Fn&& fn) {
+    const bool walls = c.wall[0] || c.wall[1] || c.wall[2];
+    return walls ? fn.template operator()<Q, S, true>() : fn.template operator()<Q, S, false>();
+}
+template <int Q, class Fn>
+static cudaError_t with_storage(const LaunchCtx& c, Fn&& fn) {
+    switch (c.storage) {
+        case 0: return with_walls<Q, StoreF64>(c, fn);
+        case 1: return with_walls<Q, StoreF32>(c, fn);
+        case 2: return with_walls<Q, StoreF16>(c, fn);
+        case 3: return with_walls<Q, StoreBF16>(c, fn);
+    }
+    return cudaErrorInvalidValue;
+}
+template <class Fn>
+static cudaError_t dispatch(const LaunchCtx& c, Fn&& fn) {
+    if (c.q == 9) return with_storage<9>(c, fn);
+    if (c.q == 19) return with_storage<19>(c, fn);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adjoint_step(const LaunchCtx& c, const void* fn, const float* lam_in, float* lam_out,
+                                const float* varpi, float* grad) {
+    return dispatch(c, [&]<int Q, class S, bool W>() { return adjoint_impl<Q, S, W>(c, fn, lam_in, lam_out, varpi, grad); });
+}
+
+cudaError_t launch_flux_seed(const LaunchCtx& c, float* lam, int plane_x) {
+    const Geometry g = geom(c);
+    const dim3 blk = block_for(c.nx);
+    const dim3 grd((c.nx + blk.x - 1) / blk.x, (c.ny + blk.y - 1) / blk.y, c.nz);
+    const bool walls = c.wall[0] || c.wall[1] || c.wall[2];
+    if (c.q == 9) {
+        if (walls) k_flux_seed<9, true><<<grd, blk, 0, c.stream>>>(lam, g, plane_x);
+        else k_flux_seed<9, false><<<grd, blk, 0, c.stream>>>(lam, g, plane_x);
+    } else {
+        if (walls) k_flux_seed<19, true><<<grd, blk, 0, c.stream>>>(lam, g, plane_x);
+        else k_flux_seed<19, false><<<grd, blk, 0, c.stream>>>(lam, g, plane_x);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plane_flux(const LaunchCtx& c, int layout, const void* f, int plane_x, double* out) {
+    return dispatch(c, [&]<int Q, class S, bool W>() {
+        using C = typename S::C;
+        Phys<C> ph{C(1.0 / c.tau), C(1.0 - 0.5 / c.tau), C(c.F[0]), C(c.F[1]), Q == 9 ? C(0) : C(c.F[2])};
+        k_plane_flux<Q, S, W><<<1, 256, 0, c.stream>>>(static_cast<const typename S::T*>(f), layout, geom(c), ph,
+                                                       C(1.0 / c.scale), plane_x, out);
+        return cudaGetLastError();
+    });
+}
+
+}  // namespace hlbm
