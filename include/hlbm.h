@@ -66,6 +66,7 @@ extern "C" {
 #define HLBM_ERR_BUSY (-6)
 #define HLBM_ERR_IO (-7)          /* file open/read/write failed or bad file */
 #define HLBM_ERR_STATE (-8)       /* the call needs a setting not yet made   */
+#define HLBM_ERR_CANCELLED (-9)   /* a server request was cancelled          */
 
 /* ---- enumerations ------------------------------------------------------ */
 #define HLBM_D2Q9 9
@@ -207,6 +208,80 @@ int hlbm_adjoint_flux_grad(hlbm_t* h, long nsteps, int ckpt_every, int plane_x, 
  * synchronise. Resuming gives the same bits as an uninterrupted run. */
 int hlbm_save(hlbm_t* h, const char* path);
 int hlbm_load(hlbm_t* h, const char* path);
+
+/* ---- serving: continuous batching of many solves ------------------------ */
+/*
+ * A server advances many independent D3Q19 HBGK solves (fully periodic
+ * lattices of any size) together. Requests wait in a first-come first-served
+ * queue and are admitted as slots while their device memory fits the budget;
+ * each pump round advances every live slot by check_every time steps in
+ * batched persistent launches (one CUDA graph replay), then reads a per-slot
+ * FP64 residual max|u - u_prev| over that interval and retires the slots
+ * whose residual fell below their tolerance (or that reached max_steps),
+ * freeing their memory for waiting requests. A slot's arithmetic, including
+ * its reduction, does not depend on the other slots in the batch, so a
+ * result is bit-identical alone and in a mix. Server calls may come from
+ * several host threads (an internal mutex serialises them).
+ */
+typedef struct hlbm_server hlbm_server_t;
+
+typedef struct {
+    int nx, ny, nz;      /* lattice edge lengths (periodic on every axis)      */
+    double tau;          /* relaxation time (> 1/2)                            */
+    double F[3];         /* body force                                         */
+    const float* varpi;  /* host, nx*ny*nz values in [0, 1]; copied at submit  */
+    double tol;          /* converged when max|u - u_prev| over one interval < tol */
+    long long max_steps; /* give up (HLBM_ERR_NOT_CONVERGED) after this many    */
+    float* u_out;        /* optional host buffer of 3*cells floats that receives
+                            the final velocity ([3][z][y][x]) at retirement;
+                            must stay valid until the result is polled; or NULL */
+    uint64_t tag;        /* caller's label, returned in the result             */
+} hlbm_request;
+
+typedef struct {
+    uint64_t id, tag;
+    int status;          /* HLBM_OK (converged), HLBM_ERR_NOT_CONVERGED,
+                            HLBM_ERR_CANCELLED or HLBM_ERR_OOM                 */
+    int nx, ny, nz;
+    long long steps;     /* time steps run                                     */
+    double k_app;        /* nu * mean(rho u_x) / F_x at the end                */
+    double max_du;       /* last residual                                      */
+    double max_u, mass, plane_flux;
+    double t_submit, t_admit, t_finish; /* seconds since server creation (host
+                                           steady clock); t_admit < 0 if never admitted */
+} hlbm_result;
+
+typedef struct {
+    int active, waiting, done_unpolled;
+    size_t mem_used, mem_budget;
+    long long lattice_updates; /* cell updates performed by all rounds        */
+    long long rounds;
+    double elapsed_s;
+} hlbm_server_stats;
+
+/* Create a server whose slots use `storage` (HLBM_F32, HLBM_F16DEV or
+ * HLBM_BF16DEV) within mem_budget bytes of device memory, checking every
+ * check_every (even, 2..10000) steps, on `cuda_stream`. */
+int hlbm_server_create(hlbm_server_t** out, size_t mem_budget, int storage, int check_every,
+                       void* cuda_stream);
+/* Queue a request (validated and copied); *id receives its identifier.
+ * HLBM_ERR_OOM if it could never fit the budget. */
+int hlbm_server_submit(hlbm_server_t* s, const hlbm_request* r, uint64_t* id);
+/* One scheduling round: admit, run check_every steps of all live slots,
+ * check, retire. Synchronises. *active / *waiting (may be NULL) receive the
+ * counts after the round. A round with no live slot launches nothing. */
+int hlbm_server_pump(hlbm_server_t* s, int* active, int* waiting);
+/* Move up to max finished results into out; *n receives how many. */
+int hlbm_server_poll(hlbm_server_t* s, hlbm_result* out, int max, int* n);
+/* Cancel a waiting (immediately) or live (at the next round) request. */
+int hlbm_server_cancel(hlbm_server_t* s, uint64_t id);
+/* Counters of the server. */
+int hlbm_server_info(hlbm_server_t* s, hlbm_server_stats* out);
+/* Fault injection for tests: the next n slot allocations fail as if the
+ * device were out of memory (admission then backs off). */
+int hlbm_server_inject_alloc_failures(hlbm_server_t* s, int n);
+/* Free the server, its slots and its queued requests (results not polled are lost). */
+void hlbm_server_destroy(hlbm_server_t* s);
 
 /* ---- misc -------------------------------------------------------------- */
 

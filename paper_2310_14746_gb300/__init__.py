@@ -34,6 +34,7 @@ HLBM_ERR_TIMEOUT = -5
 HLBM_ERR_BUSY = -6
 HLBM_ERR_IO = -7
 HLBM_ERR_STATE = -8
+HLBM_ERR_CANCELLED = -9
 
 HLBM_D2Q9 = 9
 HLBM_D3Q19 = 19
@@ -71,6 +72,34 @@ class hlbm_stats(ctypes.Structure):
                 "max_du": self.max_du, "max_u": self.max_u, "step": int(self.step)}
 
 
+class hlbm_request(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("tau", ctypes.c_double), ("F", ctypes.c_double * 3),
+                ("varpi", ctypes.c_void_p), ("tol", ctypes.c_double), ("max_steps", ctypes.c_longlong),
+                ("u_out", ctypes.c_void_p), ("tag", ctypes.c_uint64)]
+
+
+class hlbm_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int),
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("steps", ctypes.c_longlong), ("k_app", ctypes.c_double), ("max_du", ctypes.c_double),
+                ("max_u", ctypes.c_double), ("mass", ctypes.c_double), ("plane_flux", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_finish", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: (list(getattr(self, k)) if k == "F" else getattr(self, k)) for k, _ in self._fields_}
+
+
+class hlbm_server_stats(ctypes.Structure):
+    _fields_ = [("active", ctypes.c_int), ("waiting", ctypes.c_int), ("done_unpolled", ctypes.c_int),
+                ("mem_used", ctypes.c_size_t), ("mem_budget", ctypes.c_size_t),
+                ("lattice_updates", ctypes.c_longlong), ("rounds", ctypes.c_longlong),
+                ("elapsed_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _L = None
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
@@ -98,6 +127,14 @@ SIGNATURES = {
     "hlbm_adjoint_flux_grad": (_i, [_vp, ctypes.c_long, _i, _i, ctypes.POINTER(_d), _vp, _i]),
     "hlbm_save": (_i, [_vp, ctypes.c_char_p]),
     "hlbm_load": (_i, [_vp, ctypes.c_char_p]),
+    "hlbm_server_create": (_i, [ctypes.POINTER(_vp), ctypes.c_size_t, _i, _i, _vp]),
+    "hlbm_server_submit": (_i, [_vp, ctypes.POINTER(hlbm_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "hlbm_server_pump": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "hlbm_server_poll": (_i, [_vp, ctypes.POINTER(hlbm_result), _i, ctypes.POINTER(_i)]),
+    "hlbm_server_cancel": (_i, [_vp, ctypes.c_uint64]),
+    "hlbm_server_info": (_i, [_vp, ctypes.POINTER(hlbm_server_stats)]),
+    "hlbm_server_inject_alloc_failures": (_i, [_vp, _i]),
+    "hlbm_server_destroy": (None, [_vp]),
     "hlbm_strerror": (ctypes.c_char_p, [_i]),
     "hlbm_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -280,6 +317,51 @@ def hlbm_save(h, path):
 
 def hlbm_load(h, path):
     _check(_lib().hlbm_load(h, os.fsencode(path)), "hlbm_load")
+
+
+def hlbm_server_create(mem_budget, storage=HLBM_F16DEV, check_every=100, stream=None):
+    h = _vp()
+    st = current_stream() if stream is None else stream
+    _check(_lib().hlbm_server_create(ctypes.byref(h), int(mem_budget), storage, check_every, st),
+           "hlbm_server_create")
+    return h.value
+
+
+def hlbm_server_submit(s, req):
+    rid = ctypes.c_uint64(0)
+    _check(_lib().hlbm_server_submit(s, ctypes.byref(req), ctypes.byref(rid)), "hlbm_server_submit")
+    return rid.value
+
+
+def hlbm_server_pump(s):
+    a, w = _i(0), _i(0)
+    _check(_lib().hlbm_server_pump(s, ctypes.byref(a), ctypes.byref(w)), "hlbm_server_pump")
+    return a.value, w.value
+
+
+def hlbm_server_poll(s, max_results=1024):
+    buf = (hlbm_result * max_results)()
+    n = _i(0)
+    _check(_lib().hlbm_server_poll(s, buf, max_results, ctypes.byref(n)), "hlbm_server_poll")
+    return [buf[k].as_dict() for k in range(n.value)]
+
+
+def hlbm_server_cancel(s, rid):
+    _check(_lib().hlbm_server_cancel(s, int(rid)), "hlbm_server_cancel")
+
+
+def hlbm_server_info(s):
+    st = hlbm_server_stats()
+    _check(_lib().hlbm_server_info(s, ctypes.byref(st)), "hlbm_server_info")
+    return st.as_dict()
+
+
+def hlbm_server_inject_alloc_failures(s, n):
+    _check(_lib().hlbm_server_inject_alloc_failures(s, int(n)), "hlbm_server_inject_alloc_failures")
+
+
+def hlbm_server_destroy(s):
+    _lib().hlbm_server_destroy(s)
 
 
 def hlbm_strerror(status):

@@ -208,6 +208,7 @@ const char* hlbm_strerror(int status) {
         case HLBM_ERR_BUSY: return "busy";
         case HLBM_ERR_IO: return "I/O error";
         case HLBM_ERR_STATE: return "invalid state for this call";
+        case HLBM_ERR_CANCELLED: return "cancelled";
     }
     return "unknown status";
 }

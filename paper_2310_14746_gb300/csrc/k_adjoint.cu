@@ -39,19 +39,20 @@ k_adjoint_step(const typename S::T* __restrict__ fn, const float* __restrict__ l
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const Nbr nb(g, x, y, z);
-    const size_t cell = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * (size_t)z);
+    const Nbr<long long> nb(g, x, y, z);
+    const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
     const size_t N = g.N;
 
     // forward quantities at g = S f^n
     C d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = S::load(fn, gather_index<Q, WALLS>(g, nb, cell, i, NATURAL), inv_s);
-    C drho, mx, my, mz;
-    moments<Q, C>(d, ph, drho, mx, my, mz);
+    C drho, jx, jy, jz;
+    moments<Q, C>(d, drho, jx, jy, jz);
     const C rho = C(1) + drho;
     const C inv_rho = C(1) / rho;
-    const C ux = mx * inv_rho, uy = my * inv_rho, uz = mz * inv_rho;
+    C ux, uy, uz;
+    velocity<C>(jx, jy, jz, inv_rho, ph, ux, uy, uz);
     const C vp = C(__ldg(varpi + cell));
     const C vx = vp * ux, vy = vp * uy, vz = vp * uz;
     const C vv = vx * vx + vy * vy + vz * vz;
@@ -93,8 +94,9 @@ k_adjoint_step(const typename S::T* __restrict__ fn, const float* __restrict__ l
         const C mu = keep * lam[k] + a_rho + C(L::cx(k)) * ajx + C(L::cy(k)) * ajy + C(L::cz(k)) * ajz;
         // (S^T mu)_k(y) = mu_k(y + c_k): mu_k(x) goes to y = x - c_k, or, when x - c_k
         // lies beyond a wall, to slot opp(k) of x itself.
-        const bool wall = WALLS && nb.beyond_wall<Q>(k, -1);
-        const size_t dst = wall ? (size_t)opp<Q>(k) * N + cell : (size_t)k * N + nb.cell_at<Q>(g, k, -1);
+        const bool wall = WALLS && nb.template beyond_wall<Q>(k, -1);
+        const long long dst = wall ? (long long)opp<Q>(k) * (long long)N + cell
+                                   : (long long)k * (long long)N + cell + nb.template offset<Q>(k, -1);
         lam_out[dst] = float(mu);
     }
 }
@@ -108,17 +110,17 @@ __global__ void __launch_bounds__(256) k_flux_seed(float* lam, Geometry g, int p
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const Nbr nb(g, x, y, z);
-    const size_t cell = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * (size_t)z);
+    const Nbr<long long> nb(g, x, y, z);
+    const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
         // (S^T e)_k(y) = e_k(y + c_k), or e_opp(k)(y) across a wall
         float v;
-        if (WALLS && nb.beyond_wall<Q>(k, +1)) {
+        if (WALLS && nb.template beyond_wall<Q>(k, +1)) {
             v = (x == plane_x) ? float(L::cx(opp<Q>(k))) : 0.0f;
         } else {
             const int dx = L::cx(k);
-            const int xs = dx > 0 ? nb.xp : (dx < 0 ? nb.xm : x);
+            const int xs = dx > 0 ? (x == g.nx - 1 ? 0 : x + 1) : (dx < 0 ? (x == 0 ? g.nx - 1 : x - 1) : x);
             v = (xs == plane_x) ? float(dx) : 0.0f;
         }
         lam[(size_t)k * g.N + cell] = v;
@@ -137,14 +139,14 @@ k_plane_flux(const typename S::T* f, int lay, Geometry g, Phys<typename S::C> ph
     const int rows = g.ny * g.nz;
     for (int r = threadIdx.x; r < rows; r += blockDim.x) {
         const int y = r % g.ny, z = r / g.ny;
-        const Nbr nb(g, plane_x, y, z);
-        const size_t cell = (size_t)plane_x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * (size_t)z);
+        const Nbr<long long> nb(g, plane_x, y, z);
+        const long long cell = (long long)plane_x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
         C d[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) d[i] = S::load(f, gather_index<Q, WALLS>(g, nb, cell, i, lay), inv_s);
-        C drho, mx, my, mz;
-        moments<Q, C>(d, ph, drho, mx, my, mz);
-        acc += (double)mx;
+        C drho, jx, jy, jz;
+        moments<Q, C>(d, drho, jx, jy, jz);
+        acc += (double)jx + 0.5 * (double)ph.Fx;
     }
     sh[threadIdx.x] = acc;
     __syncthreads();
@@ -160,7 +162,7 @@ static cudaError_t adjoint_impl(const LaunchCtx& c, const void* fn, const float*
                                 const float* varpi, float* grad) {
     using C = typename S::C;
     const Geometry g = geom(c);
-    Phys<C> ph{C(1.0 / c.tau), C(1.0 - 0.5 / c.tau), C(c.F[0]), C(c.F[1]), Q == 9 ? C(0) : C(c.F[2])};
+    const Phys<C> ph = make_phys<C, Q>(c.tau, c.F);
     const dim3 blk = block_for(c.nx);
     const dim3 grd((c.nx + blk.x - 1) / blk.x, (c.ny + blk.y - 1) / blk.y, c.nz);
     k_adjoint_step<Q, S, WALLS><<<grd, blk, 0, c.stream>>>(static_cast<const typename S::T*>(fn), lam_in, lam_out,
@@ -213,7 +215,7 @@ cudaError_t launch_flux_seed(const LaunchCtx& c, float* lam, int plane_x) {
 cudaError_t launch_plane_flux(const LaunchCtx& c, int layout, const void* f, int plane_x, double* out) {
     return dispatch(c, [&]<int Q, class S, bool W>() {
         using C = typename S::C;
-        Phys<C> ph{C(1.0 / c.tau), C(1.0 - 0.5 / c.tau), C(c.F[0]), C(c.F[1]), Q == 9 ? C(0) : C(c.F[2])};
+        const Phys<C> ph = make_phys<C, Q>(c.tau, c.F);
         k_plane_flux<Q, S, W><<<1, 256, 0, c.stream>>>(static_cast<const typename S::T*>(f), layout, geom(c), ph,
                                                        C(1.0 / c.scale), plane_x, out);
         return cudaGetLastError();

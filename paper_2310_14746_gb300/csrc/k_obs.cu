@@ -17,7 +17,7 @@ static Geometry geom(const LaunchCtx& c) {
 
 template <class C, int Q>
 static Phys<C> phys(const LaunchCtx& c) {
-    return Phys<C>{C(1.0 / c.tau), C(1.0 - 0.5 / c.tau), C(c.F[0]), C(c.F[1]), Q == 9 ? C(0) : C(c.F[2])};
+    return make_phys<C, Q>(c.tau, c.F);
 }
 
 // ---------------------------------------------------------------------------
@@ -32,20 +32,21 @@ k_moments(const typename S::T* f, int lay, Geometry g, Phys<typename S::C> ph, t
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const Nbr nb(g, x, y, z);
-    const size_t cell = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * (size_t)z);
+    const Nbr<long long> nb(g, x, y, z);
+    const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
     C d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = S::load(f, gather_index<Q, WALLS>(g, nb, cell, i, lay), inv_s);
-    C drho, mx, my, mz;
-    moments<Q, C>(d, ph, drho, mx, my, mz);
+    C drho, jx, jy, jz;
+    moments<Q, C>(d, drho, jx, jy, jz);
     const C r = C(1) + drho;
     if (rho) rho[cell] = Out(r);
     if (u) {
-        const C inv = C(1) / r;
-        u[cell] = Out(mx * inv);
-        u[g.N + cell] = Out(my * inv);
-        u[2 * g.N + cell] = Out(mz * inv);
+        C ux, uy, uz;
+        velocity<C>(jx, jy, jz, C(1) / r, ph, ux, uy, uz);
+        u[cell] = Out(ux);
+        u[g.N + cell] = Out(uy);
+        u[2 * g.N + cell] = Out(uz);
     }
 }
 
@@ -93,20 +94,22 @@ k_reduce_partials(const typename S::T* f, int lay, Geometry g, Phys<typename S::
     const int z = blockIdx.z;
     double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (x < g.nx && y < g.ny) {
-        const Nbr nb(g, x, y, z);
-        const size_t cell = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * (size_t)z);
+        const Nbr<long long> nb(g, x, y, z);
+        const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
         C d[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) d[i] = S::load(f, gather_index<Q, WALLS>(g, nb, cell, i, lay), inv_s);
-        C drho, mx, my, mz;
-        moments<Q, C>(d, ph, drho, mx, my, mz);
-        const C inv = C(1) / (C(1) + drho);
-        const C u3[3] = {mx * inv, my * inv, mz * inv};
+        C drho, jx, jy, jz;
+        moments<Q, C>(d, drho, jx, jy, jz);
+        C u3[3];
+        velocity<C>(jx, jy, jz, C(1) / (C(1) + drho), ph, u3[0], u3[1], u3[2]);
+        // rho*u = j + F/2, formed in FP64
+        const double mx = (double)jx + 0.5 * (double)ph.Fx;
         v[0] = (double)drho;
-        v[1] = (double)mx;
-        v[2] = (double)my;
-        v[3] = (double)mz;
-        v[4] = (x == g.nx - 1) ? (double)mx : 0.0;
+        v[1] = mx;
+        v[2] = (double)jy + 0.5 * (double)ph.Fy;
+        v[3] = (double)jz + 0.5 * (double)ph.Fz;
+        v[4] = (x == g.nx - 1) ? mx : 0.0;
         double du = 0.0, um = 0.0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -197,8 +200,8 @@ k_write_state(const double* fnat, int uniform, int lay, Geometry g, typename S::
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const Nbr nb(g, x, y, z);
-    const size_t cell = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * (size_t)z);
+    const Nbr<long long> nb(g, x, y, z);
+    const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const double fi = uniform ? fnat[i] : fnat[(size_t)i * g.N + cell];
@@ -214,8 +217,8 @@ k_read_state(const typename S::T* f, int lay, Geometry g, typename S::C inv_s, d
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const Nbr nb(g, x, y, z);
-    const size_t cell = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * (size_t)z);
+    const Nbr<long long> nb(g, x, y, z);
+    const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
 #pragma unroll
     for (int i = 0; i < Q; ++i)
         fnat[(size_t)i * g.N + cell] =

@@ -12,7 +12,7 @@
 
 namespace hlbm {
 
-template <int Q, class S, bool WALLS, int MODE>
+template <int Q, class S, bool WALLS, int MODE, class I>
 __global__ void __launch_bounds__(256)
 k_step(const typename S::T* fin, typename S::T* fout, const float* __restrict__ varpi,
        Geometry g, Phys<typename S::C> ph, typename S::C s, typename S::C inv_s) {
@@ -21,8 +21,8 @@ k_step(const typename S::T* fin, typename S::T* fout, const float* __restrict__ 
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const Nbr nb(g, x, y, z);
-    const size_t cell = (size_t)x + (size_t)g.nx * ((size_t)y + (size_t)g.ny * (size_t)z);
+    const Nbr<I> nb(g, x, y, z);
+    const I cell = (I)x + (I)g.nx * ((I)y + (I)g.ny * (I)z);
     constexpr int lay_in = MODE == MODE_TWO_LATTICE ? NATURAL : (MODE == MODE_AA_EVEN ? STREAMED : SWAPPED);
     constexpr int lay_out = MODE == MODE_TWO_LATTICE ? NATURAL : (MODE == MODE_AA_EVEN ? SWAPPED : STREAMED);
 
@@ -42,13 +42,13 @@ static dim3 block_for(int nx) {
     return dim3(bx, 256 / bx, 1);
 }
 
-template <int Q, class S, bool WALLS>
+template <int Q, class S, bool WALLS, class I>
 static cudaError_t step_impl(const LaunchCtx& c, int mode, const void* fin, void* fout,
                              const float* varpi) {
     using C = typename S::C;
     using T = typename S::T;
     Geometry g{c.nx, c.ny, c.nz, c.wall[0], c.wall[1], c.wall[2], (size_t)c.nx * c.ny * c.nz};
-    Phys<C> ph{C(1.0 / c.tau), C(1.0 - 0.5 / c.tau), C(c.F[0]), C(c.F[1]), Q == 9 ? C(0) : C(c.F[2])};
+    const Phys<C> ph = make_phys<C, Q>(c.tau, c.F);
     const dim3 blk = block_for(c.nx);
     const dim3 grd((c.nx + blk.x - 1) / blk.x, (c.ny + blk.y - 1) / blk.y, c.nz);
     const C s = C(c.scale), inv_s = C(1.0 / c.scale);
@@ -56,13 +56,13 @@ static cudaError_t step_impl(const LaunchCtx& c, int mode, const void* fin, void
     T* b = static_cast<T*>(fout);
     switch (mode) {
         case MODE_TWO_LATTICE:
-            k_step<Q, S, WALLS, MODE_TWO_LATTICE><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s);
+            k_step<Q, S, WALLS, MODE_TWO_LATTICE, I><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s);
             break;
         case MODE_AA_EVEN:
-            k_step<Q, S, WALLS, MODE_AA_EVEN><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s);
+            k_step<Q, S, WALLS, MODE_AA_EVEN, I><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s);
             break;
         case MODE_AA_ODD:
-            k_step<Q, S, WALLS, MODE_AA_ODD><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s);
+            k_step<Q, S, WALLS, MODE_AA_ODD, I><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s);
             break;
         default:
             return cudaErrorInvalidValue;
@@ -73,8 +73,13 @@ static cudaError_t step_impl(const LaunchCtx& c, int mode, const void* fin, void
 template <int Q, class S>
 static cudaError_t step_w(const LaunchCtx& c, int mode, const void* fin, void* fout, const float* varpi) {
     const bool walls = c.wall[0] || c.wall[1] || c.wall[2];
-    return walls ? step_impl<Q, S, true>(c, mode, fin, fout, varpi)
-                 : step_impl<Q, S, false>(c, mode, fin, fout, varpi);
+    // 32-bit element indices while every index of the [q][cells] array fits
+    const bool small = (size_t)Q * c.nx * c.ny * c.nz < ((size_t)1 << 31);
+    if (small)
+        return walls ? step_impl<Q, S, true, int>(c, mode, fin, fout, varpi)
+                     : step_impl<Q, S, false, int>(c, mode, fin, fout, varpi);
+    return walls ? step_impl<Q, S, true, long long>(c, mode, fin, fout, varpi)
+                 : step_impl<Q, S, false, long long>(c, mode, fin, fout, varpi);
 }
 
 template <int Q>

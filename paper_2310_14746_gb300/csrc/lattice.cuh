@@ -9,6 +9,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cstddef>
+#include <cmath>
 #include <cstdint>
 
 namespace hlbm {
@@ -77,24 +78,30 @@ struct StoreF64 {
     using T = double;
     using C = double;
     static constexpr int kind = 0;
-    __device__ __forceinline__ static C load(const T* p, size_t i, C) { return __ldg(p + i); }
-    __device__ __forceinline__ static void store(T* p, size_t i, C v, C) { p[i] = v; }
+    template <class I>
+    __device__ __forceinline__ static C load(const T* p, I i, C) { return __ldg(p + i); }
+    template <class I>
+    __device__ __forceinline__ static void store(T* p, I i, C v, C) { p[i] = v; }
 };
 struct StoreF32 {
     using T = float;
     using C = float;
     static constexpr int kind = 1;
-    __device__ __forceinline__ static C load(const T* p, size_t i, C) { return __ldg(p + i); }
-    __device__ __forceinline__ static void store(T* p, size_t i, C v, C) { p[i] = v; }
+    template <class I>
+    __device__ __forceinline__ static C load(const T* p, I i, C) { return __ldg(p + i); }
+    template <class I>
+    __device__ __forceinline__ static void store(T* p, I i, C v, C) { p[i] = v; }
 };
 struct StoreF16 {
     using T = __half;
     using C = float;
     static constexpr int kind = 2;
-    __device__ __forceinline__ static C load(const T* p, size_t i, C inv_s) {
+    template <class I>
+    __device__ __forceinline__ static C load(const T* p, I i, C inv_s) {
         return __half2float(__ldg(p + i)) * inv_s;
     }
-    __device__ __forceinline__ static void store(T* p, size_t i, C v, C s) {
+    template <class I>
+    __device__ __forceinline__ static void store(T* p, I i, C v, C s) {
         p[i] = __float2half_rn(v * s);
     }
 };
@@ -102,10 +109,12 @@ struct StoreBF16 {
     using T = __nv_bfloat16;
     using C = float;
     static constexpr int kind = 3;
-    __device__ __forceinline__ static C load(const T* p, size_t i, C inv_s) {
+    template <class I>
+    __device__ __forceinline__ static C load(const T* p, I i, C inv_s) {
         return __bfloat162float(__ldg(p + i)) * inv_s;
     }
-    __device__ __forceinline__ static void store(T* p, size_t i, C v, C s) {
+    template <class I>
+    __device__ __forceinline__ static void store(T* p, I i, C v, C s) {
         p[i] = __float2bfloat16_rn(v * s);
     }
 };
@@ -125,22 +134,23 @@ struct Geometry {
     size_t N;                    // cells
 };
 
-// Neighbour bookkeeping of one cell: coordinates of x - 1 / x + 1 (periodic
-// wrap) along each axis, and whether the step crosses a wall.
+// Neighbour bookkeeping of one cell: element offsets from the cell to its
+// periodic neighbours at -1 / +1 along each axis (wrap folded in), and
+// whether the cell sits at the low / high end of a wall axis. I is the index
+// type: int when q*cells < 2^31 (cheaper address arithmetic), else long long.
+template <class I = long long>
 struct Nbr {
-    int x, y, z, xm, xp, ym, yp, zm, zp;
-    bool lo_x, hi_x, lo_y, hi_y, lo_z, hi_z;  // at the low / high end of a wall axis
+    I oxm, oxp, oym, oyp, ozm, ozp;
+    bool lo_x, hi_x, lo_y, hi_y, lo_z, hi_z;
 
-    __device__ __forceinline__ Nbr(const Geometry& g, int x_, int y_, int z_) {
-        x = x_;
-        y = y_;
-        z = z_;
-        xm = x == 0 ? g.nx - 1 : x - 1;
-        xp = x == g.nx - 1 ? 0 : x + 1;
-        ym = y == 0 ? g.ny - 1 : y - 1;
-        yp = y == g.ny - 1 ? 0 : y + 1;
-        zm = z == 0 ? g.nz - 1 : z - 1;
-        zp = z == g.nz - 1 ? 0 : z + 1;
+    __device__ __forceinline__ Nbr(const Geometry& g, int x, int y, int z) {
+        const I sy = (I)g.nx, sz = (I)g.nx * (I)g.ny;
+        oxm = x == 0 ? (I)(g.nx - 1) : (I)-1;
+        oxp = x == g.nx - 1 ? (I)(1 - g.nx) : (I)1;
+        oym = y == 0 ? (I)(g.ny - 1) * sy : -sy;
+        oyp = y == g.ny - 1 ? (I)(1 - g.ny) * sy : sy;
+        ozm = z == 0 ? (I)(g.nz - 1) * sz : -sz;
+        ozp = z == g.nz - 1 ? (I)(1 - g.nz) * sz : sz;
         lo_x = g.wall_x && x == 0;
         hi_x = g.wall_x && x == g.nx - 1;
         lo_y = g.wall_y && y == 0;
@@ -149,15 +159,19 @@ struct Nbr {
         hi_z = g.wall_z && z == g.nz - 1;
     }
 
-    // Cell index of x + s*c_i (s = -1 pull source, +1 push target) with wrap.
+    // Offset from the cell to x + s*c_i (s = -1 pull source, +1 push target).
     template <int Q>
-    __device__ __forceinline__ size_t cell_at(const Geometry& g, int i, int s) const {
+    __device__ __forceinline__ I offset(int i, int s) const {
         using L = Lat<Q>;
         const int dx = s * L::cx(i), dy = s * L::cy(i), dz = s * L::cz(i);
-        const int sx = dx > 0 ? xp : (dx < 0 ? xm : x);
-        const int sy = dy > 0 ? yp : (dy < 0 ? ym : y);
-        const int sz = dz > 0 ? zp : (dz < 0 ? zm : z);
-        return (size_t)sx + (size_t)g.nx * ((size_t)sy + (size_t)g.ny * (size_t)sz);
+        I o = 0;
+        if (dx > 0) o += oxp;
+        if (dx < 0) o += oxm;
+        if (dy > 0) o += oyp;
+        if (dy < 0) o += oym;
+        if (dz > 0) o += ozp;
+        if (dz < 0) o += ozm;
+        return o;
     }
 
     // Does x + s*c_i lie beyond a wall?
@@ -172,89 +186,174 @@ struct Nbr {
 
 // Flat index (into the [q][cells] array) holding g_i(x), the population the
 // collision at x consumes, for a state in layout `lay`.
-template <int Q, bool WALLS>
-__device__ __forceinline__ size_t gather_index(const Geometry& g, const Nbr& nb, size_t cell,
-                                               int i, int lay) {
-    const size_t N = g.N;
-    if (lay == STREAMED) return (size_t)i * N + cell;
-    const bool wall = WALLS && nb.beyond_wall<Q>(i, -1);
+template <int Q, bool WALLS, class I>
+__device__ __forceinline__ I gather_index(const Geometry& g, const Nbr<I>& nb, I cell, int i, int lay) {
+    const I N = (I)g.N;
+    if (lay == STREAMED) return (I)i * N + cell;
+    const bool wall = WALLS && nb.template beyond_wall<Q>(i, -1);
     if (lay == NATURAL)
-        return wall ? (size_t)opp<Q>(i) * N + cell : (size_t)i * N + nb.cell_at<Q>(g, i, -1);
+        return wall ? (I)opp<Q>(i) * N + cell : (I)i * N + cell + nb.template offset<Q>(i, -1);
     // SWAPPED: f_i(x - c_i) sits in slot opp(i) of cell x - c_i; across a
     // wall the bounce-back f_opp(i)(x) sits in slot i of x.
-    return wall ? (size_t)i * N + cell : (size_t)opp<Q>(i) * N + nb.cell_at<Q>(g, i, -1);
+    return wall ? (I)i * N + cell : (I)opp<Q>(i) * N + cell + nb.template offset<Q>(i, -1);
 }
 
 // Flat index of the post-collision f_i(x) for a state in layout `lay`.
-template <int Q, bool WALLS>
-__device__ __forceinline__ size_t natural_index(const Geometry& g, const Nbr& nb, size_t cell,
-                                                int i, int lay) {
-    const size_t N = g.N;
-    if (lay == NATURAL) return (size_t)i * N + cell;
-    if (lay == SWAPPED) return (size_t)opp<Q>(i) * N + cell;
+template <int Q, bool WALLS, class I>
+__device__ __forceinline__ I natural_index(const Geometry& g, const Nbr<I>& nb, I cell, int i, int lay) {
+    const I N = (I)g.N;
+    if (lay == NATURAL) return (I)i * N + cell;
+    if (lay == SWAPPED) return (I)opp<Q>(i) * N + cell;
     // STREAMED: f_i(x) travelled to x + c_i (slot i), or bounced back into
     // slot opp(i) of x when x + c_i lies beyond a wall.
-    const bool wall = WALLS && nb.beyond_wall<Q>(i, +1);
-    return wall ? (size_t)opp<Q>(i) * N + cell : (size_t)i * N + nb.cell_at<Q>(g, i, +1);
+    const bool wall = WALLS && nb.template beyond_wall<Q>(i, +1);
+    return wall ? (I)opp<Q>(i) * N + cell : (I)i * N + cell + nb.template offset<Q>(i, +1);
 }
 
 // ---------------------------------------------------------------------------
 // Per-cell physics in arithmetic type C.
+//
+// Rounding. In FP32 two habits bias the momentum budget systematically
+// (measured at ~1e-5 relative velocity error after 1000 steps of a forced
+// sphere-pack flow): (a) adding a constant (F/2, a force term) to a value
+// gives the same rounding error for every value of a binade, so it does not
+// average out; (b) per-direction constants such as w_i*omega*3, each rounded
+// on its own, make the equilibrium's first moment differ from the omega in
+// (1 - omega) by a fixed factor. So: the force never enters j; the linear
+// (odd) part of each pair is one fma with a varying product; and its
+// coefficients are derived from the rounded omega and guo so that
+// sum_i c_ix^2 k_i = omega and sum_i c_ix^2 g_i = guo hold exactly.
 // ---------------------------------------------------------------------------
 template <class C>
 struct Phys {
-    C omega;       // 1/tau
-    C guo;         // 1 - 1/(2 tau)
+    C omega;       // 1/tau, rounded to C
+    C guo;         // 1 - omega/2 (exact in C)
+    C k1, k2;      // odd equilibrium coefficients of |c|^2 = 1 and 2 directions (~3 w omega)
+    C g1, g2;      // odd force coefficients (~3 w guo)
     C Fx, Fy, Fz;  // body force
 };
 
-// Moments of deviations d_i = g_i - w_i: drho = sum d, j = sum c d (the
-// weights carry no momentum), rho = 1 + drho, rho*u = j + F/2.
+// Coefficients k1 (|c|^2 = 1, na directions along an axis) and k2 (|c|^2 = 2,
+// nb of them touch an axis) with na*k1 + nb*k2 == target exactly (checked in
+// double for float; FP64 keeps the plain rounding, its bias is at 1e-16).
+template <class C>
+__host__ inline void split_exact(C target, double w1x3, double w2x3, int na, int nb, C& k1, C& k2) {
+    const C base = C((double)target * w2x3);
+    if (sizeof(C) == 4) {
+        // try base, base+1ulp, base-1ulp, base+2ulp, ... until the split is exact
+        for (int k = 0; k < 64; ++k) {
+            const int off = (k + 1) / 2 * ((k & 1) ? 1 : -1);
+            float t2 = (float)base;
+            for (int s = 0; s < (off < 0 ? -off : off); ++s) t2 = nextafterf(t2, off > 0 ? 1e30f : -1e30f);
+            const float t1 = (float)(((double)target - nb * (double)t2) / na);
+            if ((double)na * (double)t1 + (double)nb * (double)t2 == (double)target) {
+                k1 = C(t1);
+                k2 = C(t2);
+                return;
+            }
+        }
+    }
+    k2 = base;
+    k1 = C(((double)target - nb * (double)base) / na);
+}
+
+template <class C, int Q>
+__host__ inline Phys<C> make_phys(double tau, const double F[3]) {
+    Phys<C> p;
+    p.omega = C(1.0 / tau);
+    p.guo = C(1) - p.omega / C(2);
+    // x-momentum: D3Q19 has 2 faces and 8 edges with c_x != 0 (w = 1/18, 1/36);
+    // D2Q9 has 2 faces and 4 diagonals (w = 1/9, 1/36).
+    const double w1x3 = Q == 19 ? 3.0 / 18.0 : 3.0 / 9.0, w2x3 = 3.0 / 36.0;
+    const int nb = Q == 19 ? 8 : 4;
+    split_exact<C>(p.omega, w1x3, w2x3, 2, nb, p.k1, p.k2);
+    split_exact<C>(p.guo, w1x3, w2x3, 2, nb, p.g1, p.g2);
+    p.Fx = C(F[0]);
+    p.Fy = C(F[1]);
+    p.Fz = Q == 9 ? C(0) : C(F[2]);
+    return p;
+}
+
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+
+// Zeroth and first moments of deviations d_i = g_i - w_i (Def. moments): drho =
+// sum d, j = sum c d (the weights carry no momentum); rho = 1 + drho and the
+// half-force momentum is rho*u = j + F/2 (added by the caller in the precision it needs).
 template <int Q, class C>
-__device__ __forceinline__ void moments(const C* d, const Phys<C>& ph, C& drho, C& mx, C& my,
-                                        C& mz) {
+__device__ __forceinline__ void moments(const C* d, C& drho, C& jx, C& jy, C& jz) {
     using L = Lat<Q>;
-    C s = 0, jx = 0, jy = 0, jz = 0;
+    C s = 0, ax = 0, ay = 0, az = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         s += d[i];
-        if (L::cx(i) > 0) jx += d[i];
-        if (L::cx(i) < 0) jx -= d[i];
-        if (L::cy(i) > 0) jy += d[i];
-        if (L::cy(i) < 0) jy -= d[i];
-        if (L::cz(i) > 0) jz += d[i];
-        if (L::cz(i) < 0) jz -= d[i];
+        if (L::cx(i) > 0) ax += d[i];
+        if (L::cx(i) < 0) ax -= d[i];
+        if (L::cy(i) > 0) ay += d[i];
+        if (L::cy(i) < 0) ay -= d[i];
+        if (L::cz(i) > 0) az += d[i];
+        if (L::cz(i) < 0) az -= d[i];
     }
     drho = s;
-    mx = jx + C(0.5) * ph.Fx;
-    my = jy + C(0.5) * ph.Fy;
-    mz = jz + C(0.5) * ph.Fz;
+    jx = ax;
+    jy = ay;
+    jz = az;
+}
+
+// Half-force velocity u = (j + F/2)/rho, with F/2 folded in by an fma.
+template <class C>
+__device__ __forceinline__ void velocity(C jx, C jy, C jz, C inv_rho, const Phys<C>& ph, C& ux, C& uy, C& uz) {
+    const C h = C(0.5) * inv_rho;
+    ux = fma_(ph.Fx, h, jx * inv_rho);
+    uy = fma_(ph.Fy, h, jy * inv_rho);
+    uz = fma_(ph.Fz, h, jz * inv_rho);
 }
 
 // HBGK collision of one cell, in place on the deviations d (Sec. 3.2:
 // relaxation toward the Maxwellian at varpi*u; Guo's source built with u).
+// Opposite directions share the even part of the equilibrium and of the
+// source and differ in the sign of the odd part, so each pair costs one
+// evaluation:
+//   M_i - w_i = w_i [drho + rho (4.5 (c.v)^2 - 1.5 v.v)]  +-  3 w_i rho (c.v)
+//   S_i       = guo w_i [9 (c.u)(c.F) - 3 u.F]            +-  3 w_i guo (c.F)
+// and with rho (c.v) = varpi (c.j + c.F/2) the odd part of omega*M_i + S_i is
+//   k_i varpi (c.j) + (k_i varpi / 2 + g_i) (c.F).
 template <int Q, class C>
 __device__ __forceinline__ void collide(C* d, C varpi, const Phys<C>& ph) {
     using L = Lat<Q>;
-    C drho, mx, my, mz;
-    moments<Q, C>(d, ph, drho, mx, my, mz);
+    C drho, jx, jy, jz;
+    moments<Q, C>(d, drho, jx, jy, jz);
     const C rho = C(1) + drho;
     const C inv_rho = C(1) / rho;
-    const C ux = mx * inv_rho, uy = my * inv_rho, uz = mz * inv_rho;
+    C ux, uy, uz;
+    velocity<C>(jx, jy, jz, inv_rho, ph, ux, uy, uz);
     const C vx = varpi * ux, vy = varpi * uy, vz = varpi * uz;
-    const C vv15 = C(1.5) * (vx * vx + vy * vy + vz * vz);
+    const C A = fma_(-rho, C(1.5) * (vx * vx + vy * vy + vz * vz), drho);
     const C uF3 = C(3) * (ux * ph.Fx + uy * ph.Fy + uz * ph.Fz);
+    const C r45 = C(4.5) * rho;
+    const C keep = C(1) - ph.omega;
+    {  // rest population
+        const C w = C(L::w(0));
+        d[0] = fma_(keep, d[0], fma_(ph.omega * w, A, -(ph.guo * w) * uF3));
+    }
+    const C kv1 = ph.k1 * varpi, kv2 = ph.k2 * varpi;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int i = 1; i < Q; ++i) {
+        const int j = opp<Q>(i);
+        if (j < i) continue;  // each pair once, from its lower index
+        const int c2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
         const C cx = C(L::cx(i)), cy = C(L::cy(i)), cz = C(L::cz(i));
         const C w = C(L::w(i));
         const C cv = cx * vx + cy * vy + cz * vz;
         const C cu = cx * ux + cy * uy + cz * uz;
         const C cF = cx * ph.Fx + cy * ph.Fy + cz * ph.Fz;
-        // deviation of the equilibrium from w_i
-        const C eq = w * (drho + rho * (C(3) * cv + C(4.5) * cv * cv - vv15));
-        const C src = ph.guo * w * (C(3) * cF - uF3 + C(9) * cu * cF);
-        d[i] = d[i] + ph.omega * (eq - d[i]) + src;
+        const C cj = cx * jx + cy * jy + cz * jz;
+        const C kv = c2 == 1 ? kv1 : kv2;
+        const C g = c2 == 1 ? ph.g1 : ph.g2;
+        const C even = fma_(ph.omega * w, fma_(r45, cv * cv, A), (ph.guo * w) * fma_(C(9) * cu, cF, -uF3));
+        const C odd = fma_(kv, cj, fma_(kv, C(0.5) * cF, g * cF));
+        d[i] = fma_(keep, d[i], even) + odd;
+        d[j] = fma_(keep, d[j], even) - odd;
     }
 }
 

@@ -1,0 +1,678 @@
+// Continuous-batching solve server: many D3Q19 HBGK lattices of different sizes
+// advance together in batched persistent launches.
+//
+// Each admitted request owns a slot: two population buffers (two-lattice
+// streaming), its porosity field, and its residual reference velocity. A
+// device slot table lists the live slots with their tile ranges; one launch of
+// the batched kernel advances every slot by one time step, its blocks striding
+// over all tiles of all slots. check_every launches are captured once in a
+// CUDA graph that reads the table from device memory, so admissions and
+// retirements only rewrite the table. After each graph replay a per-slot FP64
+// reduction (fixed partition per slot, so a slot's result does not depend on
+// its neighbours in the batch) gives the residual and the apparent
+// permeability; converged slots retire and free their memory, and waiting
+// requests are admitted first-come first-served while they fit the memory
+// budget.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/hlbm.h"
+#include "internal.h"
+#include "lattice.cuh"
+
+namespace hlbm {
+namespace srv {
+
+constexpr int kMaxSlots = 1024;
+constexpr int kTileX = 32, kTileY = 8;
+
+struct DevSlot {
+    void* f[2];
+    float* varpi;
+    float* u_prev;
+    int nx, ny, nz;
+    int tiles_x, tiles_y;
+    int tile_begin;
+    int ntiles;
+    Phys<float> ph;
+    double nu, Fx64;
+};
+
+struct DevTable {
+    int nslots;
+    int total_tiles;
+    int pad[2];
+    DevSlot slot[kMaxSlots];
+};
+
+__device__ __forceinline__ int find_slot(const DevTable* tab, int t, int ns) {
+    int lo = 0, hi = ns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab->slot[mid].tile_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One time step of every live slot; launch k of a check interval reads f[k&1]
+// and writes f[(k+1)&1] (each interval has an even number of steps).
+template <class S>
+__global__ void __launch_bounds__(kTileX * kTileY)
+k_batched_step(const DevTable* __restrict__ tab, int k, float s, float inv_s) {
+    using C = typename S::C;
+    using T = typename S::T;
+    const int total = tab->total_tiles;
+    const int ns = tab->nslots;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const DevSlot& sl = tab->slot[find_slot(tab, t, ns)];
+        const int lt = t - sl.tile_begin;
+        const int tx = lt % sl.tiles_x;
+        const int rest = lt / sl.tiles_x;
+        const int ty = rest % sl.tiles_y;
+        const int z = rest / sl.tiles_y;
+        const int x = tx * kTileX + threadIdx.x;
+        const int y = ty * kTileY + threadIdx.y;
+        if (x >= sl.nx || y >= sl.ny) continue;
+        const Geometry g{sl.nx, sl.ny, sl.nz, 0, 0, 0, (size_t)sl.nx * sl.ny * sl.nz};
+        const Phys<C> ph = sl.ph;
+        const T* fin = static_cast<const T*>(sl.f[k & 1]);
+        T* fout = static_cast<T*>(sl.f[(k + 1) & 1]);
+        const Nbr<int> nb(g, x, y, z);
+        const int cell = x + g.nx * (y + g.ny * z);
+        C d[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) d[i] = S::load(fin, gather_index<19, false>(g, nb, cell, i, NATURAL), inv_s);
+        collide<19, C>(d, C(__ldg(sl.varpi + cell)), ph);
+#pragma unroll
+        for (int i = 0; i < 19; ++i) S::store(fout, i * (int)g.N + cell, d[i], s);
+    }
+}
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double wmax(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Per-tile FP64 partials of the diagnostics (one block per tile of any slot).
+template <class S>
+__global__ void __launch_bounds__(kTileX * kTileY)
+k_batched_partials(const DevTable* __restrict__ tab, float inv_s, double* __restrict__ partials) {
+    using C = typename S::C;
+    using T = typename S::T;
+    __shared__ double sh[8][8];
+    const int t = blockIdx.x;
+    const DevSlot& sl = tab->slot[find_slot(tab, t, tab->nslots)];
+    const int lt = t - sl.tile_begin;
+    const int tx = lt % sl.tiles_x;
+    const int rest = lt / sl.tiles_x;
+    const int ty = rest % sl.tiles_y;
+    const int z = rest / sl.tiles_y;
+    const int x = tx * kTileX + threadIdx.x;
+    const int y = ty * kTileY + threadIdx.y;
+    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (x < sl.nx && y < sl.ny) {
+        const Geometry g{sl.nx, sl.ny, sl.nz, 0, 0, 0, (size_t)sl.nx * sl.ny * sl.nz};
+        const Phys<C> ph = sl.ph;
+        const T* f = static_cast<const T*>(sl.f[0]);
+        const Nbr<int> nb(g, x, y, z);
+        const int cell = x + g.nx * (y + g.ny * z);
+        C d[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) d[i] = S::load(f, gather_index<19, false>(g, nb, cell, i, NATURAL), inv_s);
+        C drho, jx, jy, jz;
+        moments<19, C>(d, drho, jx, jy, jz);
+        C u3[3];
+        velocity<C>(jx, jy, jz, C(1) / (C(1) + drho), ph, u3[0], u3[1], u3[2]);
+        const double mx = (double)jx + 0.5 * (double)ph.Fx;
+        v[0] = drho;
+        v[1] = mx;
+        v[2] = (double)jy + 0.5 * (double)ph.Fy;
+        v[3] = (double)jz + 0.5 * (double)ph.Fz;
+        v[4] = (x == g.nx - 1) ? mx : 0.0;
+        double du = 0.0, um = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            du = fmax(du, fabs((double)u3[c] - (double)sl.u_prev[c * g.N + cell]));
+            um = fmax(um, fabs((double)u3[c]));
+            sl.u_prev[c * g.N + cell] = u3[c];
+        }
+        v[6] = du;
+        v[7] = um;
+    }
+    const int tid = threadIdx.x + kTileX * threadIdx.y;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = c >= 6 ? wmax(v[c]) : wsum(v[c]);
+    if ((tid & 31) == 0)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) sh[tid >> 5][c] = v[c];
+    __syncthreads();
+    if (tid < 8) {
+        double a = sh[0][tid];
+        for (int w = 1; w < 8; ++w) a = tid >= 6 ? fmax(a, sh[w][tid]) : a + sh[w][tid];
+        partials[(size_t)t * 8 + tid] = a;
+    }
+}
+
+// One block per slot folds that slot's tile partials in a fixed order.
+__global__ void __launch_bounds__(256)
+k_batched_final(const DevTable* __restrict__ tab, const double* __restrict__ partials, double* __restrict__ out) {
+    __shared__ double sh[8][256];
+    const DevSlot& sl = tab->slot[blockIdx.x];
+    const int tid = threadIdx.x;
+    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = tid; t < sl.ntiles; t += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const double p = partials[(size_t)(sl.tile_begin + t) * 8 + c];
+            v[c] = c >= 6 ? fmax(v[c], p) : v[c] + p;
+        }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sh[c][tid] = v[c];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (tid < s)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) sh[c][tid] = c >= 6 ? fmax(sh[c][tid], sh[c][tid + s]) : sh[c][tid] + sh[c][tid + s];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const double cells = (double)sl.nx * sl.ny * sl.nz;
+        double* o = out + (size_t)blockIdx.x * 8;
+        o[0] = cells + sh[0][0];
+        o[1] = sh[1][0];
+        o[2] = sh[2][0];
+        o[3] = sh[3][0];
+        o[4] = sh[4][0];
+        o[5] = sl.Fx64 != 0.0 ? sl.nu * (sh[1][0] / cells) / sl.Fx64 : 0.0;
+        o[6] = sh[6][0];
+        o[7] = sh[7][0];
+    }
+}
+
+template <class S>
+static void* step_kernel_ptr() {
+    return (void*)k_batched_step<S>;
+}
+
+}  // namespace srv
+}  // namespace hlbm
+
+using namespace hlbm;
+using namespace hlbm::srv;
+
+namespace {
+
+thread_local char g_srv_err[256] = "";
+
+int srv_cuda_fail(cudaError_t e) {
+    std::snprintf(g_srv_err, sizeof(g_srv_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? HLBM_ERR_OOM : HLBM_ERR_CUDA;
+}
+
+#define SRV_CUDA(call)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return srv_cuda_fail(e_); \
+    } while (0)
+
+struct Pending {
+    uint64_t id;
+    hlbm_request req;
+    float* field = nullptr;  // pinned host copy of varpi
+    double t_submit = 0.0;
+};
+
+struct Live {
+    Pending p;
+    DevSlot ds;
+    size_t bytes = 0;
+    long long steps = 0;
+    double t_admit = 0.0;
+    bool cancel = false;
+};
+
+double feq_rest(int i) {
+    // lattice weights of D3Q19 in the documented order: rest 1/3, faces 1/18, edges 1/36
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+}  // namespace
+
+struct hlbm_server {
+    int storage = HLBM_F16DEV;
+    int check_every = 100;
+    size_t budget = 0, used = 0;
+    cudaStream_t stream = nullptr, cap_stream = nullptr;
+    int device = 0;
+    double scale = 1.0;
+    std::mutex mu;
+    std::deque<Pending> waiting;
+    std::vector<Live> live;
+    std::deque<hlbm_result> done;
+    DevTable* dtab = nullptr;
+    DevTable* htab = nullptr;
+    bool table_dirty = true;
+    cudaGraphExec_t gexec = nullptr;
+    int grid = 0;
+    double* dpartials = nullptr;
+    size_t partial_cap = 0;  // tiles
+    double* dout = nullptr;
+    double* hout = nullptr;
+    double* dfeq = nullptr;
+    uint64_t next_id = 1;
+    std::chrono::steady_clock::time_point t0;
+    int inject_alloc_failures = 0;
+    long long lups = 0;  // lattice updates done
+    long long rounds = 0;
+
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    size_t slot_bytes(const hlbm_request& r) const {
+        const size_t n = (size_t)r.nx * r.ny * r.nz;
+        return 2 * 19 * n * storage_bytes(storage) + n * sizeof(float) * 4;
+    }
+    LaunchCtx ctx_for(const Live& l) const {
+        LaunchCtx c;
+        c.q = 19;
+        c.storage = storage;
+        c.nx = l.ds.nx;
+        c.ny = l.ds.ny;
+        c.nz = l.ds.nz;
+        c.wall[0] = c.wall[1] = c.wall[2] = 0;
+        c.tau = l.p.req.tau;
+        c.F[0] = l.p.req.F[0];
+        c.F[1] = l.p.req.F[1];
+        c.F[2] = l.p.req.F[2];
+        c.scale = scale;
+        c.stream = stream;
+        return c;
+    }
+};
+
+namespace {
+
+void free_slot(hlbm_server_t* s, Live& l) {
+    cudaFreeAsync(l.ds.f[0], s->stream);
+    cudaFreeAsync(l.ds.f[1], s->stream);
+    cudaFreeAsync(l.ds.varpi, s->stream);
+    cudaFreeAsync(l.ds.u_prev, s->stream);
+    s->used -= l.bytes;
+}
+
+void finish(hlbm_server_t* s, Live& l, int status, const double* o) {
+    hlbm_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.id = l.p.id;
+    r.tag = l.p.req.tag;
+    r.status = status;
+    r.nx = l.ds.nx;
+    r.ny = l.ds.ny;
+    r.nz = l.ds.nz;
+    r.steps = l.steps;
+    if (o) {
+        r.mass = o[0];
+        r.plane_flux = o[4];
+        r.k_app = o[5];
+        r.max_du = o[6];
+        r.max_u = o[7];
+    }
+    r.t_submit = l.p.t_submit;
+    r.t_admit = l.t_admit;
+    r.t_finish = s->now();
+    s->done.push_back(r);
+}
+
+void finish_pending(hlbm_server_t* s, Pending& p, int status) {
+    hlbm_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.id = p.id;
+    r.tag = p.req.tag;
+    r.status = status;
+    r.nx = p.req.nx;
+    r.ny = p.req.ny;
+    r.nz = p.req.nz;
+    r.t_submit = p.t_submit;
+    r.t_admit = -1.0;
+    r.t_finish = s->now();
+    s->done.push_back(r);
+    cudaFreeHost(p.field);
+    p.field = nullptr;
+}
+
+cudaError_t alloc_or_inject(hlbm_server_t* s, void** p, size_t bytes) {
+    if (s->inject_alloc_failures > 0) {
+        --s->inject_alloc_failures;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, s->stream);
+}
+
+// Allocate and initialise a slot; returns cudaSuccess or the failing error (nothing leaked).
+cudaError_t admit(hlbm_server_t* s, Pending& p, Live& l) {
+    const hlbm_request& r = p.req;
+    const size_t n = (size_t)r.nx * r.ny * r.nz;
+    const size_t fb = 19 * n * storage_bytes(s->storage);
+    std::memset(&l.ds, 0, sizeof(l.ds));
+    void* ptrs[4] = {nullptr, nullptr, nullptr, nullptr};
+    const size_t sizes[4] = {fb, fb, n * sizeof(float), 3 * n * sizeof(float)};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = alloc_or_inject(s, &ptrs[k], sizes[k]);
+    if (e != cudaSuccess) {
+        for (void* q : ptrs)
+            if (q) cudaFreeAsync(q, s->stream);
+        return e;
+    }
+    l.p = p;
+    l.ds.f[0] = ptrs[0];
+    l.ds.f[1] = ptrs[1];
+    l.ds.varpi = static_cast<float*>(ptrs[2]);
+    l.ds.u_prev = static_cast<float*>(ptrs[3]);
+    l.ds.nx = r.nx;
+    l.ds.ny = r.ny;
+    l.ds.nz = r.nz;
+    l.ds.tiles_x = (r.nx + kTileX - 1) / kTileX;
+    l.ds.tiles_y = (r.ny + kTileY - 1) / kTileY;
+    l.ds.ntiles = l.ds.tiles_x * l.ds.tiles_y * r.nz;
+    l.ds.ph = make_phys<float, 19>(r.tau, r.F);
+    l.ds.nu = (r.tau - 0.5) / 3.0;
+    l.ds.Fx64 = r.F[0];
+    l.bytes = s->slot_bytes(r);
+    l.steps = 0;
+    l.t_admit = s->now();
+    e = cudaMemcpyAsync(l.ds.varpi, p.field, n * sizeof(float), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(l.ds.u_prev, 0, 3 * n * sizeof(float), s->stream);
+    if (e == cudaSuccess) e = launch_write_state(s->ctx_for(l), 0 /*NATURAL*/, s->dfeq, 1, l.ds.f[0]);
+    if (e != cudaSuccess) {
+        for (void* q : ptrs) cudaFreeAsync(q, s->stream);
+        return e;
+    }
+    s->used += l.bytes;
+    return cudaSuccess;
+}
+
+int build_graph(hlbm_server_t* s) {
+    if (!s->cap_stream) SRV_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+    void* fn = nullptr;
+    switch (s->storage) {
+        case HLBM_F32: fn = step_kernel_ptr<StoreF32>(); break;
+        case HLBM_F16DEV: fn = step_kernel_ptr<StoreF16>(); break;
+        case HLBM_BF16DEV: fn = step_kernel_ptr<StoreBF16>(); break;
+        default: return HLBM_ERR_INVALID_ARG;
+    }
+    int per_sm = 0, sms = 0;
+    SRV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTileX * kTileY, 0));
+    SRV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
+    s->grid = std::max(1, per_sm) * sms;
+    const float sc = (float)s->scale, inv = (float)(1.0 / s->scale);
+    cudaGraph_t graph = nullptr;
+    SRV_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < s->check_every; ++k) {
+        switch (s->storage) {
+            case HLBM_F32: k_batched_step<StoreF32><<<s->grid, dim3(kTileX, kTileY), 0, s->cap_stream>>>(s->dtab, k, sc, inv); break;
+            case HLBM_F16DEV: k_batched_step<StoreF16><<<s->grid, dim3(kTileX, kTileY), 0, s->cap_stream>>>(s->dtab, k, sc, inv); break;
+            default: k_batched_step<StoreBF16><<<s->grid, dim3(kTileX, kTileY), 0, s->cap_stream>>>(s->dtab, k, sc, inv); break;
+        }
+    }
+    cudaError_t e = cudaStreamEndCapture(s->cap_stream, &graph);
+    if (e != cudaSuccess) return srv_cuda_fail(e);
+    e = cudaGraphInstantiate(&s->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return srv_cuda_fail(e);
+    return HLBM_OK;
+}
+
+int upload_table(hlbm_server_t* s) {
+    int tiles = 0;
+    s->htab->nslots = (int)s->live.size();
+    for (size_t k = 0; k < s->live.size(); ++k) {
+        s->live[k].ds.tile_begin = tiles;
+        tiles += s->live[k].ds.ntiles;
+        s->htab->slot[k] = s->live[k].ds;
+    }
+    s->htab->total_tiles = tiles;
+    if ((size_t)tiles > s->partial_cap) {
+        if (s->dpartials) cudaFreeAsync(s->dpartials, s->stream);
+        s->dpartials = nullptr;
+        s->partial_cap = 0;
+        size_t cap = std::max<size_t>((size_t)tiles * 2, 4096);
+        SRV_CUDA(cudaMallocAsync(&s->dpartials, cap * 8 * sizeof(double), s->stream));
+        s->partial_cap = cap;
+    }
+    const size_t bytes = offsetof(DevTable, slot) + sizeof(DevSlot) * s->live.size();
+    SRV_CUDA(cudaMemcpyAsync(s->dtab, s->htab, bytes, cudaMemcpyHostToDevice, s->stream));
+    s->table_dirty = false;
+    return HLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hlbm_server_create(hlbm_server_t** out, size_t mem_budget, int storage, int check_every, void* cuda_stream) {
+    if (!out) return HLBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (storage != HLBM_F32 && storage != HLBM_F16DEV && storage != HLBM_BF16DEV) return HLBM_ERR_INVALID_ARG;
+    if (check_every < 2 || check_every % 2 || check_every > 10000 || mem_budget == 0) return HLBM_ERR_INVALID_ARG;
+    hlbm_server_t* s = new (std::nothrow) hlbm_server();
+    if (!s) return HLBM_ERR_OOM;
+    s->storage = storage;
+    s->check_every = check_every;
+    s->budget = mem_budget;
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+    s->scale = storage == HLBM_F16DEV ? 4096.0 : 1.0;
+    s->t0 = std::chrono::steady_clock::now();
+    double feq[19];
+    for (int i = 0; i < 19; ++i) feq[i] = feq_rest(i);
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaMalloc(&s->dtab, sizeof(DevTable));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->htab, sizeof(DevTable));
+    if (e == cudaSuccess) e = cudaMalloc(&s->dout, kMaxSlots * 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&s->hout, kMaxSlots * 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s->dfeq, sizeof(feq));
+    if (e == cudaSuccess) e = cudaMemcpy(s->dfeq, feq, sizeof(feq), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        std::memset(s->htab, 0, sizeof(DevTable));
+        e = cudaMemcpy(s->dtab, s->htab, sizeof(DevTable), cudaMemcpyHostToDevice);
+    }
+    int rc = e == cudaSuccess ? build_graph(s) : srv_cuda_fail(e);
+    if (rc != HLBM_OK) {
+        hlbm_server_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return HLBM_OK;
+}
+
+void hlbm_server_destroy(hlbm_server_t* s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    for (Live& l : s->live) free_slot(s, l);
+    for (Pending& p : s->waiting) cudaFreeHost(p.field);
+    if (s->dpartials) cudaFreeAsync(s->dpartials, s->stream);
+    cudaStreamSynchronize(s->stream);
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    cudaFree(s->dtab);
+    cudaFree(s->dout);
+    cudaFree(s->dfeq);
+    if (s->htab) cudaFreeHost(s->htab);
+    if (s->hout) cudaFreeHost(s->hout);
+    delete s;
+}
+
+int hlbm_server_submit(hlbm_server_t* s, const hlbm_request* r, uint64_t* id) {
+    if (!s || !r || !r->varpi) return HLBM_ERR_INVALID_ARG;
+    if (r->nx < 1 || r->ny < 1 || r->nz < 1 || !(r->tau > 0.5) || !std::isfinite(r->tau)) return HLBM_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(r->F[a])) return HLBM_ERR_INVALID_ARG;
+    if (!(r->tol > 0.0) || r->max_steps < 1) return HLBM_ERR_INVALID_ARG;
+    const size_t n = (size_t)r->nx * r->ny * r->nz;
+    if (n > ((size_t)1 << 31) / 19) return HLBM_ERR_INVALID_ARG;
+    for (size_t k = 0; k < n; ++k)
+        if (!(r->varpi[k] >= 0.0f && r->varpi[k] <= 1.0f)) return HLBM_ERR_INVALID_ARG;
+    if (s->slot_bytes(*r) > s->budget) return HLBM_ERR_OOM;
+    Pending p;
+    p.req = *r;
+    if (cudaMallocHost(&p.field, n * sizeof(float)) != cudaSuccess) return HLBM_ERR_OOM;
+    std::memcpy(p.field, r->varpi, n * sizeof(float));
+    p.req.varpi = nullptr;
+    std::lock_guard<std::mutex> lk(s->mu);
+    p.id = s->next_id++;
+    p.t_submit = s->now();
+    s->waiting.push_back(p);
+    if (id) *id = p.id;
+    return HLBM_OK;
+}
+
+int hlbm_server_cancel(hlbm_server_t* s, uint64_t id) {
+    if (!s) return HLBM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto it = s->waiting.begin(); it != s->waiting.end(); ++it)
+        if (it->id == id) {
+            finish_pending(s, *it, HLBM_ERR_CANCELLED);
+            s->waiting.erase(it);
+            return HLBM_OK;
+        }
+    for (Live& l : s->live)
+        if (l.p.id == id) {
+            l.cancel = true;
+            return HLBM_OK;
+        }
+    return HLBM_ERR_INVALID_ARG;
+}
+
+int hlbm_server_inject_alloc_failures(hlbm_server_t* s, int n) {
+    if (!s || n < 0) return HLBM_ERR_INVALID_ARG;
+    s->inject_alloc_failures = n;
+    return HLBM_OK;
+}
+
+int hlbm_server_pump(hlbm_server_t* s, int* active, int* waiting) {
+    if (!s) return HLBM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    // 1. admission, first come first served, while the memory budget allows
+    while (!s->waiting.empty() && s->live.size() < (size_t)kMaxSlots) {
+        Pending& p = s->waiting.front();
+        if (s->used + s->slot_bytes(p.req) > s->budget) break;
+        Live l;
+        cudaError_t e = admit(s, p, l);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            if (s->live.empty()) {  // nothing will free memory: fail the request
+                finish_pending(s, p, HLBM_ERR_OOM);
+                s->waiting.pop_front();
+                continue;
+            }
+            break;  // back off until a slot retires
+        }
+        if (e != cudaSuccess) return srv_cuda_fail(e);
+        s->live.push_back(l);
+        s->waiting.pop_front();
+        s->table_dirty = true;
+    }
+    if (!s->live.empty()) {
+        if (s->table_dirty) {
+            int rc = upload_table(s);
+            if (rc != HLBM_OK) return rc;
+        }
+        // 2. check_every batched steps of every live slot
+        SRV_CUDA(cudaGraphLaunch(s->gexec, s->stream));
+        // 3. per-slot FP64 diagnostics
+        const float inv = (float)(1.0 / s->scale);
+        const int tiles = s->htab->total_tiles;
+        switch (s->storage) {
+            case HLBM_F32: k_batched_partials<StoreF32><<<tiles, dim3(kTileX, kTileY), 0, s->stream>>>(s->dtab, inv, s->dpartials); break;
+            case HLBM_F16DEV: k_batched_partials<StoreF16><<<tiles, dim3(kTileX, kTileY), 0, s->stream>>>(s->dtab, inv, s->dpartials); break;
+            default: k_batched_partials<StoreBF16><<<tiles, dim3(kTileX, kTileY), 0, s->stream>>>(s->dtab, inv, s->dpartials); break;
+        }
+        SRV_CUDA(cudaGetLastError());
+        const int ns = (int)s->live.size();
+        k_batched_final<<<ns, 256, 0, s->stream>>>(s->dtab, s->dpartials, s->dout);
+        SRV_CUDA(cudaGetLastError());
+        SRV_CUDA(cudaMemcpyAsync(s->hout, s->dout, (size_t)ns * 8 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        SRV_CUDA(cudaStreamSynchronize(s->stream));
+        s->rounds++;
+        // 4. retire converged / exhausted / cancelled slots
+        std::vector<Live> keep;
+        keep.reserve(s->live.size());
+        for (int k = 0; k < ns; ++k) {
+            Live& l = s->live[k];
+            l.steps += s->check_every;
+            s->lups += (long long)s->check_every * l.ds.nx * l.ds.ny * l.ds.nz;
+            const double* o = s->hout + (size_t)k * 8;
+            int status = 1;
+            if (l.cancel) status = HLBM_ERR_CANCELLED;
+            else if (o[6] < l.p.req.tol) status = HLBM_OK;
+            else if (l.steps >= l.p.req.max_steps) status = HLBM_ERR_NOT_CONVERGED;
+            if (status == 1) {
+                keep.push_back(l);
+                continue;
+            }
+            if (l.p.req.u_out && status != HLBM_ERR_CANCELLED) {
+                const size_t n = (size_t)l.ds.nx * l.ds.ny * l.ds.nz;
+                void* du = nullptr;
+                cudaError_t e = cudaMallocAsync(&du, 3 * n * sizeof(float), s->stream);
+                if (e == cudaSuccess) e = launch_moments(s->ctx_for(l), 0, l.ds.f[0], nullptr, du, 0);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(l.p.req.u_out, du, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
+                if (du) cudaFreeAsync(du, s->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+                if (e != cudaSuccess) return srv_cuda_fail(e);
+            }
+            finish(s, l, status, o);
+            free_slot(s, l);
+            cudaFreeHost(l.p.field);
+            s->table_dirty = true;
+        }
+        s->live.swap(keep);
+    }
+    if (active) *active = (int)s->live.size();
+    if (waiting) *waiting = (int)s->waiting.size();
+    return HLBM_OK;
+}
+
+int hlbm_server_poll(hlbm_server_t* s, hlbm_result* out, int max, int* n) {
+    if (!s || !n || (max > 0 && !out) || max < 0) return HLBM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    int k = 0;
+    while (k < max && !s->done.empty()) {
+        out[k++] = s->done.front();
+        s->done.pop_front();
+    }
+    *n = k;
+    return HLBM_OK;
+}
+
+int hlbm_server_info(hlbm_server_t* s, hlbm_server_stats* out) {
+    if (!s || !out) return HLBM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->active = (int)s->live.size();
+    out->waiting = (int)s->waiting.size();
+    out->done_unpolled = (int)s->done.size();
+    out->mem_used = s->used;
+    out->mem_budget = s->budget;
+    out->lattice_updates = s->lups;
+    out->rounds = s->rounds;
+    out->elapsed_s = s->now();
+    return HLBM_OK;
+}
+
+}  // extern "C"
