@@ -205,6 +205,61 @@ def run_reference(args, w, rank):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64):
+    """Serving stream sample: the first n_requests of the seeded trace (edges up to max_edge).
+    1) capacity: all requests at t = 0 through the batched FP16 server -> solves/s;
+    2) Poisson arrivals at 0.8x that capacity, replayed in real time through the batched server
+       and through the plain FP32 loop (one solve at a time, one launch per step);
+    returns p50/p99 time-to-steady-state of both, throughput, and the permeability difference
+    between the FP16 batched and FP32 plain results."""
+    from paper_2310_14746_gb300 import inputs
+    from paper_2310_14746_gb300 import serving as sv
+    import paper_2310_14746_gb300 as hb
+
+    base = [r for r in inputs.serving_requests(4 * n_requests, seed, rate_per_s=1.0) if r["edge"] <= max_edge]
+    base = base[:n_requests]
+    cache = {}
+
+    def field_of(rq):
+        key = (rq["edge"], rq["period"], round(rq["radius_ratio"], 12))
+        if key not in cache:
+            cache[key] = inputs.regular_sphere_field(rq["edge"], period=rq["period"], radius_ratio=rq["radius_ratio"])
+        return cache[key]
+
+    for rq in base:
+        field_of(rq)
+    res0, info0 = sv.run_stream(base, field_of, storage=hb.HLBM_F16DEV, mem_budget=budget_gb << 30, tol=tol,
+                                realtime=False)
+    cap = len(res0) / max(max(r["t_finish"] for r in res0), 1e-9)
+    rate = 0.8 * cap
+    trace = [dict(rq) for rq in base]
+    t = 0.0
+    rng = np.random.default_rng(seed + 1)
+    for rq in trace:
+        t += float(rng.exponential(1.0 / rate))
+        rq["arrival_s"] = t
+    res_b, info_b = sv.run_stream(trace, field_of, storage=hb.HLBM_F16DEV, mem_budget=budget_gb << 30, tol=tol)
+    res_p, info_p = sv.plain_loop(trace, field_of, tol=tol)
+    kb = {r["tag"]: r["k_app"] for r in res_b}
+    kp = {r["tag"]: r["k_app"] for r in res_p}
+    kerr = max(abs(kb[k] - kp[k]) / abs(kp[k]) for k in kb if k in kp and kp[k] != 0)
+    pb = sv.percentiles([r["latency_s"] for r in res_b])
+    pp = sv.percentiles([r["latency_s"] for r in res_p])
+    span_b = max(r["t_finish"] for r in res_b)
+    return {
+        "requests": len(trace), "edges": sorted({r["edge"] for r in trace}), "tol_max_du": tol,
+        "capacity_solves_per_s": cap, "arrival_rate_per_s": rate,
+        "batched_f16": {"p50_s": pb["p50_s"], "p99_s": pb["p99_s"], "solves_per_s": len(res_b) / span_b,
+                        "mlups": info_b["lattice_updates"] / info_b["elapsed_s"] / 1e6,
+                        "converged": sum(r["status"] == 0 for r in res_b)},
+        "plain_f32": {"p50_s": pp["p50_s"], "p99_s": pp["p99_s"],
+                      "solves_per_s": len(res_p) / info_p["elapsed_s"],
+                      "mlups": info_p["lattice_updates"] / info_p["elapsed_s"] / 1e6},
+        "k_app_rel_diff_f16_batched_vs_f32_plain": kerr,
+        "steps": {"min": int(min(r["steps"] for r in res_b)), "max": int(max(r["steps"] for r in res_b))},
+    }
+
+
 def run_gpu(args, w, rank, world, local_rank):
     import torch
     import paper_2310_14746_gb300 as hb
@@ -296,6 +351,12 @@ def run_gpu(args, w, rank, world, local_rank):
     kname = "stream_collide_d%dq%d_%s_%s" % (3 if q == 19 else 2, q, w["storage"], w["pattern"])
     traffic = KERNEL_TRAFFIC_BYTES.get((kname, n))
 
+    serving = None
+    if args.serving_requests > 0:
+        lat.close()
+        lat = None
+        serving = serving_leg(args.serving_requests, 2310147460 + 4, max_edge=args.serving_max_edge)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         mlups, ksteps, dt, cores = oracle_mlups(w, varpi, budget_s=args.cpu_budget)
@@ -318,9 +379,11 @@ def run_gpu(args, w, rank, world, local_rank):
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "stats": {"k_app": st["k_app"], "mass_rel_drift": st["mass"] / cells - 1.0, "max_du": st["max_du"]},
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
-    lat.close()
+    if lat is not None:
+        lat.close()
     if dist:
         dist.destroy_process_group()
 
@@ -335,6 +398,9 @@ def main():
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=0,
+                    help="also replay this many requests of the seeded serving trace (batched vs plain)")
+    ap.add_argument("--serving-max-edge", type=int, default=192)
     args = ap.parse_args()
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)

@@ -237,7 +237,12 @@ struct Pending {
     hlbm_request req;
     float* field = nullptr;  // pinned host copy of varpi
     double t_submit = 0.0;
+    int alloc_failures = 0;  // admissions that failed for lack of device memory
 };
+
+// With no live slot nothing will free memory; after this many failed
+// admissions in a row the request fails with HLBM_ERR_OOM.
+constexpr int kMaxAllocRetries = 8;
 
 struct Live {
     Pending p;
@@ -576,12 +581,12 @@ int hlbm_server_pump(hlbm_server_t* s, int* active, int* waiting) {
         cudaError_t e = admit(s, p, l);
         if (e == cudaErrorMemoryAllocation) {
             cudaGetLastError();
-            if (s->live.empty()) {  // nothing will free memory: fail the request
-                finish_pending(s, p, HLBM_ERR_OOM);
+            if (s->live.empty() && ++p.alloc_failures >= kMaxAllocRetries) {
+                finish_pending(s, p, HLBM_ERR_OOM);  // nothing will free memory
                 s->waiting.pop_front();
                 continue;
             }
-            break;  // back off until a slot retires
+            break;  // back off: retry at the next round
         }
         if (e != cudaSuccess) return srv_cuda_fail(e);
         s->live.push_back(l);

@@ -107,6 +107,26 @@ def test_memory_admission_and_fault_injection():
     assert len(ks) == 1  # identical requests, identical results
 
 
+def test_persistent_allocation_failure_fails_request():
+    """With nothing running and every allocation failing, a request is retried for a few
+    rounds and then returned with HLBM_ERR_OOM (no hang)."""
+    vp = field(32, 16, 0.3)
+    srv = Server(1 << 30, hb.HLBM_F16DEV, 100)
+    rid = srv.submit(vp, tol=1e-30, max_steps=200)
+    srv.inject_alloc_failures(1000)
+    rounds = 0
+    res = []
+    while True:
+        a, w = srv.pump()
+        res += srv.poll()
+        rounds += 1
+        if a == 0 and w == 0:
+            break
+        assert rounds < 100
+    srv.close()
+    assert [(r["id"], r["status"]) for r in res] == [(rid, hb.HLBM_ERR_OOM)]
+
+
 def test_cancel_and_invalid_requests():
     vp = field(32, 16, 0.3)
     srv = Server(1 << 30, hb.HLBM_F16DEV, 100)
