@@ -67,6 +67,8 @@ extern "C" {
 #define HLBM_ERR_IO (-7)          /* file open/read/write failed or bad file */
 #define HLBM_ERR_STATE (-8)       /* the call needs a setting not yet made   */
 #define HLBM_ERR_CANCELLED (-9)   /* a server request was cancelled          */
+#define HLBM_ERR_SCRATCH_LIMIT (-10) /* lattice too large for the fixed scratch
+                                        of hlbm_reduce_noalloc                */
 
 /* ---- enumerations ------------------------------------------------------ */
 #define HLBM_D2Q9 9
@@ -282,6 +284,34 @@ int hlbm_server_info(hlbm_server_t* s, hlbm_server_stats* out);
 int hlbm_server_inject_alloc_failures(hlbm_server_t* s, int n);
 /* Free the server, its slots and its queued requests (results not polled are lost). */
 void hlbm_server_destroy(hlbm_server_t* s);
+
+/* ---- allocation-free diagnostics --------------------------------------- */
+
+/* The diagnostics of hlbm_reduce for callers that must not allocate device
+ * memory: for example code running inside an allocator or memory-pool
+ * callback, a host application that gives the library a fixed arena and
+ * forbids further cudaMalloc calls, or a monitoring hook that must not fail
+ * for lack of memory. (The paper has no counterpart; this is a systems
+ * interface.) The caller passes everything: f, the post-collision state in
+ * the two-lattice (NATURAL) layout, q*nx*ny*nz device values of the storage
+ * type holding (f_i - w_i) * storage_scale, [q][z][y][x]; u_prev, a device
+ * buffer of 3*nx*ny*nz values in the arithmetic type (double for HLBM_F64,
+ * float otherwise) holding the previous velocity, which the call compares
+ * against (max_du) and then overwrites with the current velocity; the lattice
+ * description (velset, sizes, storage, bc[3] boundary types, tau, F[3]); and
+ * the host struct `out` (its step field is set to 0). The call uses no
+ * memory the library allocates: its scratch is a fixed 4 MiB array in the
+ * library's device memory, which every GPU that loads the library keeps
+ * until the process exits. A lattice whose reduction needs more than 65536
+ * partial blocks (blocks of 256 threads over x-rows of up to 128 cells; 256^3
+ * is the largest cube that fits) returns HLBM_ERR_SCRATCH_LIMIT. The first
+ * call on a device looks up the array's device address (once per device);
+ * make that first call before any stream capture. Every call on a device
+ * shares the array: calls whose work overlaps on the same GPU race on it, so
+ * serialise them. Synchronises `cuda_stream`. */
+int hlbm_reduce_noalloc(int velset, int nx, int ny, int nz, int storage, const int* bc, double tau,
+                        const double* F, double storage_scale, const void* f, void* u_prev,
+                        hlbm_stats* out, void* cuda_stream);
 
 /* ---- misc -------------------------------------------------------------- */
 

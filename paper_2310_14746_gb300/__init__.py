@@ -35,6 +35,7 @@ HLBM_ERR_BUSY = -6
 HLBM_ERR_IO = -7
 HLBM_ERR_STATE = -8
 HLBM_ERR_CANCELLED = -9
+HLBM_ERR_SCRATCH_LIMIT = -10
 
 HLBM_D2Q9 = 9
 HLBM_D3Q19 = 19
@@ -135,6 +136,8 @@ SIGNATURES = {
     "hlbm_server_info": (_i, [_vp, ctypes.POINTER(hlbm_server_stats)]),
     "hlbm_server_inject_alloc_failures": (_i, [_vp, _i]),
     "hlbm_server_destroy": (None, [_vp]),
+    "hlbm_reduce_noalloc": (_i, [_i, _i, _i, _i, _i, ctypes.POINTER(_i), _d, ctypes.POINTER(_d), _d, _vp, _vp,
+                                 ctypes.POINTER(hlbm_stats), _vp]),
     "hlbm_strerror": (ctypes.c_char_p, [_i]),
     "hlbm_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -362,6 +365,20 @@ def hlbm_server_inject_alloc_failures(s, n):
 
 def hlbm_server_destroy(s):
     _lib().hlbm_server_destroy(s)
+
+
+def hlbm_reduce_noalloc(velset, nx, ny, nz, storage, bc, tau, F, storage_scale, f, u_prev, stream=None):
+    """Diagnostics without any device allocation; f and u_prev are device buffers
+    (CUDA tensors or raw pointers) the caller owns. Returns the stats dict."""
+    fp = f if isinstance(f, int) else f.data_ptr()
+    up = u_prev if isinstance(u_prev, int) else u_prev.data_ptr()
+    st = hlbm_stats()
+    b = (_i * 3)(*bc)
+    FF = (_d * 3)(*F)
+    s = current_stream() if stream is None else stream
+    _check(_lib().hlbm_reduce_noalloc(velset, nx, ny, nz, storage, b, float(tau), FF, float(storage_scale), fp, up,
+                                      ctypes.byref(st), s), "hlbm_reduce_noalloc")
+    return st.as_dict()
 
 
 def hlbm_strerror(status):

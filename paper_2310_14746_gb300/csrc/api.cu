@@ -209,6 +209,7 @@ const char* hlbm_strerror(int status) {
         case HLBM_ERR_IO: return "I/O error";
         case HLBM_ERR_STATE: return "invalid state for this call";
         case HLBM_ERR_CANCELLED: return "cancelled";
+        case HLBM_ERR_SCRATCH_LIMIT: return "lattice too large for the fixed scratch of the allocation-free call";
     }
     return "unknown status";
 }
