@@ -77,6 +77,30 @@ def _env_int(name, default):
         return default
 
 
+def shard(items, rank, world):
+    """The units (requests, replicas) this rank owns: a strided split, no overlap."""
+    return list(items)[rank::world]
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """Max of a scalar over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, dist=None, device="cpu"):
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def measured_hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -205,7 +229,7 @@ def run_reference(args, w, rank):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64):
+def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, world=1, dist=None):
     """Serving stream sample: the first n_requests of the seeded trace (edges up to max_edge).
     1) capacity: all requests at t = 0 through the batched FP16 server -> solves/s;
     2) Poisson arrivals at 0.8x that capacity, replayed in real time through the batched server
@@ -217,7 +241,7 @@ def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64):
     import paper_2310_14746_gb300 as hb
 
     base = [r for r in inputs.serving_requests(4 * n_requests, seed, rate_per_s=1.0) if r["edge"] <= max_edge]
-    base = base[:n_requests]
+    base = shard(base[:n_requests], rank, world)  # requests are independent: split them over ranks
     cache = {}
 
     def field_of(rq):
@@ -246,15 +270,22 @@ def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64):
     pb = sv.percentiles([r["latency_s"] for r in res_b])
     pp = sv.percentiles([r["latency_s"] for r in res_p])
     span_b = max(r["t_finish"] for r in res_b)
+    if dist is not None:  # whole-job throughput; tail latency as the worst rank's
+        pb["p99_s"] = max_over_ranks(pb["p99_s"], dist, "cuda")
+        pp["p99_s"] = max_over_ranks(pp["p99_s"], dist, "cuda")
+        kerr = max_over_ranks(kerr, dist, "cuda")
     return {
         "requests": len(trace), "edges": sorted({r["edge"] for r in trace}), "tol_max_du": tol,
         "capacity_solves_per_s": cap, "arrival_rate_per_s": rate,
-        "batched_f16": {"p50_s": pb["p50_s"], "p99_s": pb["p99_s"], "solves_per_s": len(res_b) / span_b,
-                        "mlups": info_b["lattice_updates"] / info_b["elapsed_s"] / 1e6,
-                        "converged": sum(r["status"] == 0 for r in res_b)},
+        "batched_f16": {"p50_s": pb["p50_s"], "p99_s": pb["p99_s"],
+                        "solves_per_s": sum_over_ranks(len(res_b) / span_b, dist, "cuda"),
+                        "mlups": sum_over_ranks(info_b["lattice_updates"] / info_b["elapsed_s"] / 1e6, dist, "cuda"),
+                        "converged": sum(r["status"] == 0 for r in res_b),
+                        "refined_to_fp32": sum(r.get("final_storage") == hb.HLBM_F32 for r in res_b)},
         "plain_f32": {"p50_s": pp["p50_s"], "p99_s": pp["p99_s"],
-                      "solves_per_s": len(res_p) / info_p["elapsed_s"],
-                      "mlups": info_p["lattice_updates"] / info_p["elapsed_s"] / 1e6},
+                      "solves_per_s": sum_over_ranks(len(res_p) / info_p["elapsed_s"], dist, "cuda"),
+                      "mlups": sum_over_ranks(info_p["lattice_updates"] / info_p["elapsed_s"] / 1e6, dist, "cuda"),
+                      "converged": sum(r["status"] == 0 for r in res_p)},
         "k_app_rel_diff_f16_batched_vs_f32_plain": kerr,
         "steps": {"min": int(min(r["steps"] for r in res_b)), "max": int(max(r["steps"] for r in res_b))},
     }
@@ -320,10 +351,7 @@ def run_gpu(args, w, rank, world, local_rank):
     torch.cuda.synchronize()
     elapsed_ms = t_start.elapsed_time(t_end)
     kern_ms = sum(a.elapsed_time(b) for a, b in evs) / (args.steps * inner)
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, "cuda")
     value = world * cells * inner * args.steps / (elapsed_ms * 1e-3) / 1e6
 
     # ---- e2e through the C ABI with host buffers --------------------------------
@@ -336,11 +364,7 @@ def run_gpu(args, w, rank, world, local_rank):
         lat.step(inner)
         st_e2e = lat.reduce()                   # device -> host diagnostics
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e_value = world * cells * inner * e2e_steps / e2e_s / 1e6
     h2d = cells * 4 + q * 8
     d2h = 8 * 8
@@ -355,7 +379,8 @@ def run_gpu(args, w, rank, world, local_rank):
     if args.serving_requests > 0:
         lat.close()
         lat = None
-        serving = serving_leg(args.serving_requests, 2310147460 + 4, max_edge=args.serving_max_edge)
+        serving = serving_leg(args.serving_requests, 2310147460 + 4, max_edge=args.serving_max_edge,
+                              rank=rank, world=world, dist=dist)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -251,6 +251,8 @@ typedef struct {
     double max_u, mass, plane_flux;
     double t_submit, t_admit, t_finish; /* seconds since server creation (host
                                            steady clock); t_admit < 0 if never admitted */
+    long long steps_low; /* of `steps`, those run in the reduced-precision storage */
+    int final_storage;   /* storage the solve ended in (HLBM_F32 after refinement) */
 } hlbm_result;
 
 typedef struct {
@@ -261,11 +263,20 @@ typedef struct {
     double elapsed_s;
 } hlbm_server_stats;
 
-/* Create a server whose slots use `storage` (HLBM_F32, HLBM_F16DEV or
+/* Create a server whose slots start in `storage` (HLBM_F32, HLBM_F16DEV or
  * HLBM_BF16DEV) within mem_budget bytes of device memory, checking every
- * check_every (even, 2..10000) steps, on `cuda_stream`. */
+ * check_every (even, 2..10000) steps, on `cuda_stream`. With a reduced-
+ * precision storage, refinement is on by default: a slot whose residual
+ * reaches the storage's rounding floor (floor_coef * max|u|; 2e-3 for FP16,
+ * 1.6e-2 for BF16) or stops improving for 20 checks is converted in place to
+ * FP32 storage (when the budget allows) and must then meet its tolerance in
+ * FP32. */
 int hlbm_server_create(hlbm_server_t** out, size_t mem_budget, int storage, int check_every,
                        void* cuda_stream);
+/* Turn refinement on or off and set its floor coefficient (>= 0). With it off,
+ * a reduced-precision slot converges only if its own rounding noise stays
+ * below the tolerance. */
+int hlbm_server_set_refinement(hlbm_server_t* s, int enable, double floor_coef);
 /* Queue a request (validated and copied); *id receives its identifier.
  * HLBM_ERR_OOM if it could never fit the budget. */
 int hlbm_server_submit(hlbm_server_t* s, const hlbm_request* r, uint64_t* id);

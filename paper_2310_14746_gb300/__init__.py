@@ -85,7 +85,8 @@ class hlbm_result(ctypes.Structure):
                 ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("steps", ctypes.c_longlong), ("k_app", ctypes.c_double), ("max_du", ctypes.c_double),
                 ("max_u", ctypes.c_double), ("mass", ctypes.c_double), ("plane_flux", ctypes.c_double),
-                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_finish", ctypes.c_double)]
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_finish", ctypes.c_double),
+                ("steps_low", ctypes.c_longlong), ("final_storage", ctypes.c_int)]
 
     def as_dict(self):
         return {k: (list(getattr(self, k)) if k == "F" else getattr(self, k)) for k, _ in self._fields_}
@@ -129,6 +130,7 @@ SIGNATURES = {
     "hlbm_save": (_i, [_vp, ctypes.c_char_p]),
     "hlbm_load": (_i, [_vp, ctypes.c_char_p]),
     "hlbm_server_create": (_i, [ctypes.POINTER(_vp), ctypes.c_size_t, _i, _i, _vp]),
+    "hlbm_server_set_refinement": (_i, [_vp, _i, _d]),
     "hlbm_server_submit": (_i, [_vp, ctypes.POINTER(hlbm_request), ctypes.POINTER(ctypes.c_uint64)]),
     "hlbm_server_pump": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "hlbm_server_poll": (_i, [_vp, ctypes.POINTER(hlbm_result), _i, ctypes.POINTER(_i)]),
@@ -328,6 +330,10 @@ def hlbm_server_create(mem_budget, storage=HLBM_F16DEV, check_every=100, stream=
     _check(_lib().hlbm_server_create(ctypes.byref(h), int(mem_budget), storage, check_every, st),
            "hlbm_server_create")
     return h.value
+
+
+def hlbm_server_set_refinement(s, enable, floor_coef):
+    _check(_lib().hlbm_server_set_refinement(s, int(bool(enable)), float(floor_coef)), "hlbm_server_set_refinement")
 
 
 def hlbm_server_submit(s, req):

@@ -12,10 +12,37 @@
 
 namespace hlbm {
 
+// Base pointer of every population plane, passed by value (kernel parameter
+// space), so an access is one wide multiply-add of a 32/64-bit cell offset.
+template <class T, int Q>
+struct Planes {
+    T* p[Q];
+};
+
+// Plane and cell of g_i(x) (the population the collision at x consumes) for a
+// state in layout LAY; see gather_index in lattice.cuh for the three layouts.
+template <int Q, bool WALLS, int LAY, class T, class I>
+__device__ __forceinline__ T* gather_ptr(const Planes<T, Q>& pl, const Nbr<I>& nb, I cell, int i) {
+    if (LAY == STREAMED) return pl.p[i] + cell;
+    const bool wall = WALLS && nb.template beyond_wall<Q>(i, -1);
+    const I src = cell + nb.template offset<Q>(i, -1);
+    if (LAY == NATURAL) return wall ? pl.p[opp<Q>(i)] + cell : pl.p[i] + src;
+    return wall ? pl.p[i] + cell : pl.p[opp<Q>(i)] + src;  // SWAPPED
+}
+
+// Plane and cell that receive the post-collision f_i(x) in layout LAY.
+template <int Q, bool WALLS, int LAY, class T, class I>
+__device__ __forceinline__ T* scatter_ptr(const Planes<T, Q>& pl, const Nbr<I>& nb, I cell, int i) {
+    if (LAY == NATURAL) return pl.p[i] + cell;
+    if (LAY == SWAPPED) return pl.p[opp<Q>(i)] + cell;
+    const bool wall = WALLS && nb.template beyond_wall<Q>(i, +1);  // STREAMED
+    return wall ? pl.p[opp<Q>(i)] + cell : pl.p[i] + (cell + nb.template offset<Q>(i, +1));
+}
+
 template <int Q, class S, bool WALLS, int MODE, class I>
 __global__ void __launch_bounds__(256)
-k_step(const typename S::T* fin, typename S::T* fout, const float* __restrict__ varpi,
-       Geometry g, Phys<typename S::C> ph, typename S::C s, typename S::C inv_s) {
+k_step(Planes<const typename S::T, Q> fin, Planes<typename S::T, Q> fout, const float* __restrict__ varpi,
+       Geometry g, Phys<typename S::C> ph, typename S::C s, typename S::C inv_s, int fx_only) {
     using C = typename S::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -28,12 +55,14 @@ k_step(const typename S::T* fin, typename S::T* fout, const float* __restrict__ 
 
     C d[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = S::load(fin, gather_index<Q, WALLS>(g, nb, cell, i, lay_in), inv_s);
+    for (int i = 0; i < Q; ++i) d[i] = S::load_raw(gather_ptr<Q, WALLS, lay_in>(fin, nb, cell, i), 0);
 
-    collide<Q, C>(d, C(__ldg(varpi + cell)), ph);
+    const C vp = C(__ldg(varpi + cell));
+    if (fx_only) collide<Q, C, S::scaled, true>(d, vp, ph, s, inv_s);
+    else collide<Q, C, S::scaled, false>(d, vp, ph, s, inv_s);
 
 #pragma unroll
-    for (int i = 0; i < Q; ++i) S::store(fout, natural_index<Q, WALLS>(g, nb, cell, i, lay_out), d[i], s);
+    for (int i = 0; i < Q; ++i) S::store_raw(scatter_ptr<Q, WALLS, lay_out>(fout, nb, cell, i), 0, d[i]);
 }
 
 static dim3 block_for(int nx) {
@@ -52,17 +81,22 @@ static cudaError_t step_impl(const LaunchCtx& c, int mode, const void* fin, void
     const dim3 blk = block_for(c.nx);
     const dim3 grd((c.nx + blk.x - 1) / blk.x, (c.ny + blk.y - 1) / blk.y, c.nz);
     const C s = C(c.scale), inv_s = C(1.0 / c.scale);
-    const T* a = static_cast<const T*>(fin);
-    T* b = static_cast<T*>(fout);
+    Planes<const T, Q> a;
+    Planes<T, Q> b;
+    for (int i = 0; i < Q; ++i) {
+        a.p[i] = static_cast<const T*>(fin) + (size_t)i * g.N;
+        b.p[i] = static_cast<T*>(fout) + (size_t)i * g.N;
+    }
+    const int fx = (Q == 9 || c.F[2] == 0.0) && c.F[1] == 0.0;
     switch (mode) {
         case MODE_TWO_LATTICE:
-            k_step<Q, S, WALLS, MODE_TWO_LATTICE, I><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s);
+            k_step<Q, S, WALLS, MODE_TWO_LATTICE, I><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s, fx);
             break;
         case MODE_AA_EVEN:
-            k_step<Q, S, WALLS, MODE_AA_EVEN, I><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s);
+            k_step<Q, S, WALLS, MODE_AA_EVEN, I><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s, fx);
             break;
         case MODE_AA_ODD:
-            k_step<Q, S, WALLS, MODE_AA_ODD, I><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s);
+            k_step<Q, S, WALLS, MODE_AA_ODD, I><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, s, inv_s, fx);
             break;
         default:
             return cudaErrorInvalidValue;

@@ -74,10 +74,18 @@ __host__ __device__ constexpr int opp(int i) {
 // Storage policies: populations live as deviations d_i = (f_i - w_i) * s.
 // T = element type in HBM, C = arithmetic type.
 // ---------------------------------------------------------------------------
+// `scaled` policies keep deviations times a power-of-two scale s; the step
+// kernel then works in scaled units throughout (load_raw / store_raw), which
+// is exact because multiplying by a power of two commutes with rounding.
 struct StoreF64 {
     using T = double;
     using C = double;
     static constexpr int kind = 0;
+    static constexpr bool scaled = false;
+    template <class I>
+    __device__ __forceinline__ static C load_raw(const T* p, I i) { return __ldg(p + i); }
+    template <class I>
+    __device__ __forceinline__ static void store_raw(T* p, I i, C v) { p[i] = v; }
     template <class I>
     __device__ __forceinline__ static C load(const T* p, I i, C) { return __ldg(p + i); }
     template <class I>
@@ -87,6 +95,11 @@ struct StoreF32 {
     using T = float;
     using C = float;
     static constexpr int kind = 1;
+    static constexpr bool scaled = false;
+    template <class I>
+    __device__ __forceinline__ static C load_raw(const T* p, I i) { return __ldg(p + i); }
+    template <class I>
+    __device__ __forceinline__ static void store_raw(T* p, I i, C v) { p[i] = v; }
     template <class I>
     __device__ __forceinline__ static C load(const T* p, I i, C) { return __ldg(p + i); }
     template <class I>
@@ -96,6 +109,11 @@ struct StoreF16 {
     using T = __half;
     using C = float;
     static constexpr int kind = 2;
+    static constexpr bool scaled = true;
+    template <class I>
+    __device__ __forceinline__ static C load_raw(const T* p, I i) { return __half2float(__ldg(p + i)); }
+    template <class I>
+    __device__ __forceinline__ static void store_raw(T* p, I i, C v) { p[i] = __float2half_rn(v); }
     template <class I>
     __device__ __forceinline__ static C load(const T* p, I i, C inv_s) {
         return __half2float(__ldg(p + i)) * inv_s;
@@ -109,6 +127,11 @@ struct StoreBF16 {
     using T = __nv_bfloat16;
     using C = float;
     static constexpr int kind = 3;
+    static constexpr bool scaled = false;
+    template <class I>
+    __device__ __forceinline__ static C load_raw(const T* p, I i) { return __bfloat162float(__ldg(p + i)); }
+    template <class I>
+    __device__ __forceinline__ static void store_raw(T* p, I i, C v) { p[i] = __float2bfloat16_rn(v); }
     template <class I>
     __device__ __forceinline__ static C load(const T* p, I i, C inv_s) {
         return __bfloat162float(__ldg(p + i)) * inv_s;
@@ -318,25 +341,38 @@ __device__ __forceinline__ void velocity(C jx, C jy, C jz, C inv_rho, const Phys
 //   S_i       = guo w_i [9 (c.u)(c.F) - 3 u.F]            +-  3 w_i guo (c.F)
 // and with rho (c.v) = varpi (c.j + c.F/2) the odd part of omega*M_i + S_i is
 //   k_i varpi (c.j) + (k_i varpi / 2 + g_i) (c.F).
-template <int Q, class C>
-__device__ __forceinline__ void collide(C* d, C varpi, const Phys<C>& ph) {
+template <int Q, class C, bool SCALED = false, bool FX_ONLY = false>
+__device__ __forceinline__ void collide(C* d, C varpi, const Phys<C>& ph, C s = C(1), C inv_s = C(1)) {
+    // FX_ONLY: the caller guarantees F = (Fx, 0, 0); the terms with c.F = 0 drop out.
+    // With SCALED the d are s * (f - w) on entry and exit; every term below
+    // that adds into d carries the factor s (a power of two: exact).
     using L = Lat<Q>;
-    C drho, jx, jy, jz;
-    moments<Q, C>(d, drho, jx, jy, jz);
+    C drho_s, jxs, jys, jzs;  // sums in the units of d
+    moments<Q, C>(d, drho_s, jxs, jys, jzs);
+    const C drho = SCALED ? drho_s * inv_s : drho_s;
+    const C jx = SCALED ? jxs * inv_s : jxs, jy = SCALED ? jys * inv_s : jys, jz = SCALED ? jzs * inv_s : jzs;
     const C rho = C(1) + drho;
     const C inv_rho = C(1) / rho;
     C ux, uy, uz;
     velocity<C>(jx, jy, jz, inv_rho, ph, ux, uy, uz);
+    if (FX_ONLY) {
+        uy = jy * inv_rho;
+        uz = jz * inv_rho;
+    }
     const C vx = varpi * ux, vy = varpi * uy, vz = varpi * uz;
-    const C A = fma_(-rho, C(1.5) * (vx * vx + vy * vy + vz * vz), drho);
-    const C uF3 = C(3) * (ux * ph.Fx + uy * ph.Fy + uz * ph.Fz);
-    const C r45 = C(4.5) * rho;
+    const C rho_s = SCALED ? rho * s : rho;
+    const C A = fma_(-rho_s, C(1.5) * (vx * vx + vy * vy + vz * vz), drho_s);
+    const C uF3 = FX_ONLY ? C(3) * (ux * ph.Fx) : C(3) * (ux * ph.Fx + uy * ph.Fy + uz * ph.Fz);
+    const C r45 = C(4.5) * rho_s;
     const C keep = C(1) - ph.omega;
+    const C guo_s = SCALED ? ph.guo * s : ph.guo;
     {  // rest population
         const C w = C(L::w(0));
-        d[0] = fma_(keep, d[0], fma_(ph.omega * w, A, -(ph.guo * w) * uF3));
+        d[0] = fma_(keep, d[0], fma_(ph.omega * w, A, -(guo_s * w) * uF3));
     }
     const C kv1 = ph.k1 * varpi, kv2 = ph.k2 * varpi;
+    const C g1 = SCALED ? ph.g1 * s : ph.g1, g2 = SCALED ? ph.g2 * s : ph.g2;
+    const C kvs1 = SCALED ? kv1 * s : kv1, kvs2 = SCALED ? kv2 * s : kv2;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const int j = opp<Q>(i);
@@ -346,12 +382,20 @@ __device__ __forceinline__ void collide(C* d, C varpi, const Phys<C>& ph) {
         const C w = C(L::w(i));
         const C cv = cx * vx + cy * vy + cz * vz;
         const C cu = cx * ux + cy * uy + cz * uz;
-        const C cF = cx * ph.Fx + cy * ph.Fy + cz * ph.Fz;
-        const C cj = cx * jx + cy * jy + cz * jz;
+        // c.j in the units of d (scaled j when SCALED)
+        const C cj = cx * jxs + cy * jys + cz * jzs;
         const C kv = c2 == 1 ? kv1 : kv2;
-        const C g = c2 == 1 ? ph.g1 : ph.g2;
-        const C even = fma_(ph.omega * w, fma_(r45, cv * cv, A), (ph.guo * w) * fma_(C(9) * cu, cF, -uF3));
-        const C odd = fma_(kv, cj, fma_(kv, C(0.5) * cF, g * cF));
+        const C kvs = c2 == 1 ? kvs1 : kvs2;
+        const C g = c2 == 1 ? g1 : g2;
+        C even, odd;
+        if (FX_ONLY && L::cx(i) == 0) {  // c.F = 0
+            even = fma_(ph.omega * w, fma_(r45, cv * cv, A), -(guo_s * w) * uF3);
+            odd = kv * cj;
+        } else {
+            const C cF = FX_ONLY ? cx * ph.Fx : cx * ph.Fx + cy * ph.Fy + cz * ph.Fz;
+            even = fma_(ph.omega * w, fma_(r45, cv * cv, A), (guo_s * w) * fma_(C(9) * cu, cF, -uF3));
+            odd = fma_(kv, cj, fma_(kvs, C(0.5) * cF, g * cF));
+        }
         d[i] = fma_(keep, d[i], even) + odd;
         d[j] = fma_(keep, d[j], even) - odd;
     }

@@ -3,16 +3,25 @@
 //
 // Each admitted request owns a slot: two population buffers (two-lattice
 // streaming), its porosity field, and its residual reference velocity. A
-// device slot table lists the live slots with their tile ranges; one launch of
-// the batched kernel advances every slot by one time step, its blocks striding
-// over all tiles of all slots. check_every launches are captured once in a
-// CUDA graph that reads the table from device memory, so admissions and
-// retirements only rewrite the table. After each graph replay a per-slot FP64
-// reduction (fixed partition per slot, so a slot's result does not depend on
-// its neighbours in the batch) gives the residual and the apparent
-// permeability; converged slots retire and free their memory, and waiting
-// requests are admitted first-come first-served while they fit the memory
-// budget.
+// device slot table lists the live slots with their tile ranges and storage
+// type; one launch of the batched kernel advances every slot by one time
+// step, its blocks striding over all tiles of all slots (a tile never mixes
+// slots, so the storage branch is uniform per block). check_every launches
+// are captured once in a CUDA graph that reads the table from device memory,
+// so admissions, retirements and precision changes only rewrite the table.
+// After each graph replay a per-slot FP64 reduction (a fixed partition per
+// slot, so a slot's result does not depend on its neighbours in the batch)
+// gives the residual and the apparent permeability; converged slots retire
+// and free their memory, and waiting requests are admitted first-come
+// first-served while they fit the memory budget.
+//
+// Precision ladder. With FP16 or BF16 storage a slot first runs in that
+// storage (half the bytes of FP32). Reduced-precision rounding puts a floor
+// under the residual that scales with the flow speed (measured for FP16 near
+// 6e-4 * max|u|), so a fast flow can never reach an absolute tolerance of
+// 1e-6 there. When the residual reaches that floor (or stops improving), the
+// slot's state is converted in place to FP32 deviations and the solve
+// finishes in FP32 against the requested tolerance.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,6 +53,8 @@ struct DevSlot {
     int tiles_x, tiles_y;
     int tile_begin;
     int ntiles;
+    int storage;  // HLBM_F32, HLBM_F16DEV or HLBM_BF16DEV
+    float scale, inv_scale;
     Phys<float> ph;
     double nu, Fx64;
 };
@@ -65,13 +76,27 @@ __device__ __forceinline__ int find_slot(const DevTable* tab, int t, int ns) {
     return lo;
 }
 
-// One time step of every live slot; launch k of a check interval reads f[k&1]
+// One cell update of a slot in storage S; launch k of an interval reads f[k&1]
 // and writes f[(k+1)&1] (each interval has an even number of steps).
 template <class S>
-__global__ void __launch_bounds__(kTileX * kTileY)
-k_batched_step(const DevTable* __restrict__ tab, int k, float s, float inv_s) {
+__device__ __forceinline__ void advance_cell(const DevSlot& sl, int k, int x, int y, int z) {
     using C = typename S::C;
     using T = typename S::T;
+    const Geometry g{sl.nx, sl.ny, sl.nz, 0, 0, 0, (size_t)sl.nx * sl.ny * sl.nz};
+    const Phys<C> ph = sl.ph;
+    const T* fin = static_cast<const T*>(sl.f[k & 1]);
+    T* fout = static_cast<T*>(sl.f[(k + 1) & 1]);
+    const Nbr<int> nb(g, x, y, z);
+    const int cell = x + g.nx * (y + g.ny * z);
+    C d[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) d[i] = S::load_raw(fin, gather_index<19, false>(g, nb, cell, i, NATURAL));
+    collide<19, C, S::scaled>(d, C(__ldg(sl.varpi + cell)), ph, C(sl.scale), C(sl.inv_scale));
+#pragma unroll
+    for (int i = 0; i < 19; ++i) S::store_raw(fout, i * (int)g.N + cell, d[i]);
+}
+
+__global__ void __launch_bounds__(kTileX * kTileY) k_batched_step(const DevTable* __restrict__ tab, int k) {
     const int total = tab->total_tiles;
     const int ns = tab->nslots;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -84,18 +109,11 @@ k_batched_step(const DevTable* __restrict__ tab, int k, float s, float inv_s) {
         const int x = tx * kTileX + threadIdx.x;
         const int y = ty * kTileY + threadIdx.y;
         if (x >= sl.nx || y >= sl.ny) continue;
-        const Geometry g{sl.nx, sl.ny, sl.nz, 0, 0, 0, (size_t)sl.nx * sl.ny * sl.nz};
-        const Phys<C> ph = sl.ph;
-        const T* fin = static_cast<const T*>(sl.f[k & 1]);
-        T* fout = static_cast<T*>(sl.f[(k + 1) & 1]);
-        const Nbr<int> nb(g, x, y, z);
-        const int cell = x + g.nx * (y + g.ny * z);
-        C d[19];
-#pragma unroll
-        for (int i = 0; i < 19; ++i) d[i] = S::load(fin, gather_index<19, false>(g, nb, cell, i, NATURAL), inv_s);
-        collide<19, C>(d, C(__ldg(sl.varpi + cell)), ph);
-#pragma unroll
-        for (int i = 0; i < 19; ++i) S::store(fout, i * (int)g.N + cell, d[i], s);
+        switch (sl.storage) {
+            case HLBM_F16DEV: advance_cell<StoreF16>(sl, k, x, y, z); break;
+            case HLBM_BF16DEV: advance_cell<StoreBF16>(sl, k, x, y, z); break;
+            default: advance_cell<StoreF32>(sl, k, x, y, z); break;
+        }
     }
 }
 
@@ -110,12 +128,44 @@ __device__ __forceinline__ double wmax(double v) {
     return v;
 }
 
-// Per-tile FP64 partials of the diagnostics (one block per tile of any slot).
+// Diagnostics of one cell of a slot in storage S into v[8] (see k_batched_partials).
 template <class S>
-__global__ void __launch_bounds__(kTileX * kTileY)
-k_batched_partials(const DevTable* __restrict__ tab, float inv_s, double* __restrict__ partials) {
+__device__ __forceinline__ void cell_stats(const DevSlot& sl, int x, int y, int z, double* v) {
     using C = typename S::C;
     using T = typename S::T;
+    const Geometry g{sl.nx, sl.ny, sl.nz, 0, 0, 0, (size_t)sl.nx * sl.ny * sl.nz};
+    const Phys<C> ph = sl.ph;
+    const T* f = static_cast<const T*>(sl.f[0]);
+    const Nbr<int> nb(g, x, y, z);
+    const int cell = x + g.nx * (y + g.ny * z);
+    C d[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) d[i] = S::load(f, gather_index<19, false>(g, nb, cell, i, NATURAL), C(sl.inv_scale));
+    C drho, jx, jy, jz;
+    moments<19, C>(d, drho, jx, jy, jz);
+    C u3[3];
+    velocity<C>(jx, jy, jz, C(1) / (C(1) + drho), ph, u3[0], u3[1], u3[2]);
+    const double mx = (double)jx + 0.5 * (double)ph.Fx;
+    v[0] = drho;
+    v[1] = mx;
+    v[2] = (double)jy + 0.5 * (double)ph.Fy;
+    v[3] = (double)jz + 0.5 * (double)ph.Fz;
+    v[4] = (x == g.nx - 1) ? mx : 0.0;
+    double du = 0.0, um = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        du = fmax(du, fabs((double)u3[c] - (double)sl.u_prev[c * g.N + cell]));
+        um = fmax(um, fabs((double)u3[c]));
+        sl.u_prev[c * g.N + cell] = u3[c];
+    }
+    v[6] = du;
+    v[7] = um;
+}
+
+// Per-tile FP64 partials of the diagnostics (one block per tile of any slot):
+// sum drho, sum rho*u (3), plane flux, -, max|du|, max|u|.
+__global__ void __launch_bounds__(kTileX * kTileY)
+k_batched_partials(const DevTable* __restrict__ tab, double* __restrict__ partials) {
     __shared__ double sh[8][8];
     const int t = blockIdx.x;
     const DevSlot& sl = tab->slot[find_slot(tab, t, tab->nslots)];
@@ -128,33 +178,11 @@ k_batched_partials(const DevTable* __restrict__ tab, float inv_s, double* __rest
     const int y = ty * kTileY + threadIdx.y;
     double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (x < sl.nx && y < sl.ny) {
-        const Geometry g{sl.nx, sl.ny, sl.nz, 0, 0, 0, (size_t)sl.nx * sl.ny * sl.nz};
-        const Phys<C> ph = sl.ph;
-        const T* f = static_cast<const T*>(sl.f[0]);
-        const Nbr<int> nb(g, x, y, z);
-        const int cell = x + g.nx * (y + g.ny * z);
-        C d[19];
-#pragma unroll
-        for (int i = 0; i < 19; ++i) d[i] = S::load(f, gather_index<19, false>(g, nb, cell, i, NATURAL), inv_s);
-        C drho, jx, jy, jz;
-        moments<19, C>(d, drho, jx, jy, jz);
-        C u3[3];
-        velocity<C>(jx, jy, jz, C(1) / (C(1) + drho), ph, u3[0], u3[1], u3[2]);
-        const double mx = (double)jx + 0.5 * (double)ph.Fx;
-        v[0] = drho;
-        v[1] = mx;
-        v[2] = (double)jy + 0.5 * (double)ph.Fy;
-        v[3] = (double)jz + 0.5 * (double)ph.Fz;
-        v[4] = (x == g.nx - 1) ? mx : 0.0;
-        double du = 0.0, um = 0.0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            du = fmax(du, fabs((double)u3[c] - (double)sl.u_prev[c * g.N + cell]));
-            um = fmax(um, fabs((double)u3[c]));
-            sl.u_prev[c * g.N + cell] = u3[c];
+        switch (sl.storage) {
+            case HLBM_F16DEV: cell_stats<StoreF16>(sl, x, y, z, v); break;
+            case HLBM_BF16DEV: cell_stats<StoreBF16>(sl, x, y, z, v); break;
+            default: cell_stats<StoreF32>(sl, x, y, z, v); break;
         }
-        v[6] = du;
-        v[7] = um;
     }
     const int tid = threadIdx.x + kTileX * threadIdx.y;
 #pragma unroll
@@ -206,9 +234,11 @@ k_batched_final(const DevTable* __restrict__ tab, const double* __restrict__ par
     }
 }
 
+// Reduced-precision deviations (times s) -> FP32 deviations, element-wise.
 template <class S>
-static void* step_kernel_ptr() {
-    return (void*)k_batched_step<S>;
+__global__ void k_widen(const typename S::T* __restrict__ in, float* __restrict__ out, size_t n, float inv_s) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = S::load(in, i, inv_s);
 }
 
 }  // namespace srv
@@ -243,13 +273,20 @@ struct Pending {
 // With no live slot nothing will free memory; after this many failed
 // admissions in a row the request fails with HLBM_ERR_OOM.
 constexpr int kMaxAllocRetries = 8;
+// A reduced-precision slot moves to FP32 once its residual is below
+// floor_coef * max|u| (or the tolerance), or has not improved by 10 % for
+// this many checks.
+constexpr int kStallChecks = 20;
 
 struct Live {
     Pending p;
     DevSlot ds;
     size_t bytes = 0;
     long long steps = 0;
+    long long steps_low = 0;  // steps run in the reduced-precision storage
     double t_admit = 0.0;
+    double best_du = 1e300;
+    int stall = 0;
     bool cancel = false;
 };
 
@@ -258,15 +295,18 @@ double feq_rest(int i) {
     return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
 }
 
+double scale_of(int storage) { return storage == HLBM_F16DEV ? 4096.0 : 1.0; }
+
 }  // namespace
 
 struct hlbm_server {
-    int storage = HLBM_F16DEV;
+    int storage = HLBM_F16DEV;  // storage new slots start in
     int check_every = 100;
+    int refine = 1;             // move reduced-precision slots to FP32 at their floor
+    double floor_coef = 2e-3;   // reduced-precision residual floor, in units of max|u|
     size_t budget = 0, used = 0;
     cudaStream_t stream = nullptr, cap_stream = nullptr;
     int device = 0;
-    double scale = 1.0;
     std::mutex mu;
     std::deque<Pending> waiting;
     std::vector<Live> live;
@@ -290,14 +330,14 @@ struct hlbm_server {
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
+    static size_t bytes_for(int st, size_t n) { return 2 * 19 * n * storage_bytes(st) + n * sizeof(float) * 4; }
     size_t slot_bytes(const hlbm_request& r) const {
-        const size_t n = (size_t)r.nx * r.ny * r.nz;
-        return 2 * 19 * n * storage_bytes(storage) + n * sizeof(float) * 4;
+        return bytes_for(storage, (size_t)r.nx * r.ny * r.nz);
     }
     LaunchCtx ctx_for(const Live& l) const {
         LaunchCtx c;
         c.q = 19;
-        c.storage = storage;
+        c.storage = l.ds.storage;
         c.nx = l.ds.nx;
         c.ny = l.ds.ny;
         c.nz = l.ds.nz;
@@ -306,7 +346,7 @@ struct hlbm_server {
         c.F[0] = l.p.req.F[0];
         c.F[1] = l.p.req.F[1];
         c.F[2] = l.p.req.F[2];
-        c.scale = scale;
+        c.scale = l.ds.scale;
         c.stream = stream;
         return c;
     }
@@ -332,6 +372,8 @@ void finish(hlbm_server_t* s, Live& l, int status, const double* o) {
     r.ny = l.ds.ny;
     r.nz = l.ds.nz;
     r.steps = l.steps;
+    r.steps_low = l.steps_low;
+    r.final_storage = l.ds.storage;
     if (o) {
         r.mass = o[0];
         r.plane_flux = o[4];
@@ -354,6 +396,7 @@ void finish_pending(hlbm_server_t* s, Pending& p, int status) {
     r.nx = p.req.nx;
     r.ny = p.req.ny;
     r.nz = p.req.nz;
+    r.final_storage = s->storage;
     r.t_submit = p.t_submit;
     r.t_admit = -1.0;
     r.t_finish = s->now();
@@ -396,6 +439,9 @@ cudaError_t admit(hlbm_server_t* s, Pending& p, Live& l) {
     l.ds.tiles_x = (r.nx + kTileX - 1) / kTileX;
     l.ds.tiles_y = (r.ny + kTileY - 1) / kTileY;
     l.ds.ntiles = l.ds.tiles_x * l.ds.tiles_y * r.nz;
+    l.ds.storage = s->storage;
+    l.ds.scale = (float)scale_of(s->storage);
+    l.ds.inv_scale = (float)(1.0 / scale_of(s->storage));
     l.ds.ph = make_phys<float, 19>(r.tau, r.F);
     l.ds.nu = (r.tau - 0.5) / 3.0;
     l.ds.Fx64 = r.F[0];
@@ -413,29 +459,57 @@ cudaError_t admit(hlbm_server_t* s, Pending& p, Live& l) {
     return cudaSuccess;
 }
 
+// Move a reduced-precision slot to FP32 storage (state converted in place).
+// Returns cudaErrorMemoryAllocation (nothing changed) when it does not fit.
+cudaError_t widen_to_fp32(hlbm_server_t* s, Live& l) {
+    const size_t n = (size_t)l.ds.nx * l.ds.ny * l.ds.nz;
+    const size_t extra = hlbm_server::bytes_for(HLBM_F32, n) - l.bytes;
+    if (s->used + extra > s->budget) return cudaErrorMemoryAllocation;
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaError_t e = alloc_or_inject(s, &a, 19 * n * sizeof(float));
+    if (e == cudaSuccess) e = alloc_or_inject(s, &b, 19 * n * sizeof(float));
+    if (e != cudaSuccess) {
+        if (a) cudaFreeAsync(a, s->stream);
+        return e;
+    }
+    const unsigned grid = (unsigned)std::min<size_t>((19 * n + 255) / 256, 152 * 16);
+    if (l.ds.storage == HLBM_F16DEV)
+        k_widen<StoreF16><<<grid, 256, 0, s->stream>>>(static_cast<const __half*>(l.ds.f[0]), static_cast<float*>(a),
+                                                       19 * n, l.ds.inv_scale);
+    else
+        k_widen<StoreBF16><<<grid, 256, 0, s->stream>>>(static_cast<const __nv_bfloat16*>(l.ds.f[0]),
+                                                        static_cast<float*>(a), 19 * n, l.ds.inv_scale);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaFreeAsync(a, s->stream);
+        cudaFreeAsync(b, s->stream);
+        return e;
+    }
+    cudaFreeAsync(l.ds.f[0], s->stream);
+    cudaFreeAsync(l.ds.f[1], s->stream);
+    l.ds.f[0] = a;
+    l.ds.f[1] = b;
+    l.ds.storage = HLBM_F32;
+    l.ds.scale = 1.0f;
+    l.ds.inv_scale = 1.0f;
+    s->used += extra;
+    l.bytes += extra;
+    l.best_du = 1e300;
+    l.stall = 0;
+    return cudaSuccess;
+}
+
 int build_graph(hlbm_server_t* s) {
     if (!s->cap_stream) SRV_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
-    void* fn = nullptr;
-    switch (s->storage) {
-        case HLBM_F32: fn = step_kernel_ptr<StoreF32>(); break;
-        case HLBM_F16DEV: fn = step_kernel_ptr<StoreF16>(); break;
-        case HLBM_BF16DEV: fn = step_kernel_ptr<StoreBF16>(); break;
-        default: return HLBM_ERR_INVALID_ARG;
-    }
     int per_sm = 0, sms = 0;
-    SRV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTileX * kTileY, 0));
+    SRV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_step, kTileX * kTileY, 0));
     SRV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
     s->grid = std::max(1, per_sm) * sms;
-    const float sc = (float)s->scale, inv = (float)(1.0 / s->scale);
     cudaGraph_t graph = nullptr;
     SRV_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < s->check_every; ++k) {
-        switch (s->storage) {
-            case HLBM_F32: k_batched_step<StoreF32><<<s->grid, dim3(kTileX, kTileY), 0, s->cap_stream>>>(s->dtab, k, sc, inv); break;
-            case HLBM_F16DEV: k_batched_step<StoreF16><<<s->grid, dim3(kTileX, kTileY), 0, s->cap_stream>>>(s->dtab, k, sc, inv); break;
-            default: k_batched_step<StoreBF16><<<s->grid, dim3(kTileX, kTileY), 0, s->cap_stream>>>(s->dtab, k, sc, inv); break;
-        }
-    }
+    for (int k = 0; k < s->check_every; ++k)
+        k_batched_step<<<s->grid, dim3(kTileX, kTileY), 0, s->cap_stream>>>(s->dtab, k);
     cudaError_t e = cudaStreamEndCapture(s->cap_stream, &graph);
     if (e != cudaSuccess) return srv_cuda_fail(e);
     e = cudaGraphInstantiate(&s->gexec, graph, 0);
@@ -482,7 +556,7 @@ int hlbm_server_create(hlbm_server_t** out, size_t mem_budget, int storage, int 
     s->check_every = check_every;
     s->budget = mem_budget;
     s->stream = static_cast<cudaStream_t>(cuda_stream);
-    s->scale = storage == HLBM_F16DEV ? 4096.0 : 1.0;
+    s->floor_coef = storage == HLBM_BF16DEV ? 1.6e-2 : 2e-3;
     s->t0 = std::chrono::steady_clock::now();
     double feq[19];
     for (int i = 0; i < 19; ++i) feq[i] = feq_rest(i);
@@ -506,10 +580,21 @@ int hlbm_server_create(hlbm_server_t** out, size_t mem_budget, int storage, int 
     return HLBM_OK;
 }
 
+int hlbm_server_set_refinement(hlbm_server_t* s, int enable, double floor_coef) {
+    if (!s || !(floor_coef >= 0.0) || !std::isfinite(floor_coef)) return HLBM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->refine = enable ? 1 : 0;
+    s->floor_coef = floor_coef;
+    return HLBM_OK;
+}
+
 void hlbm_server_destroy(hlbm_server_t* s) {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
-    for (Live& l : s->live) free_slot(s, l);
+    for (Live& l : s->live) {
+        free_slot(s, l);
+        cudaFreeHost(l.p.field);
+    }
     for (Pending& p : s->waiting) cudaFreeHost(p.field);
     if (s->dpartials) cudaFreeAsync(s->dpartials, s->stream);
     cudaStreamSynchronize(s->stream);
@@ -601,13 +686,8 @@ int hlbm_server_pump(hlbm_server_t* s, int* active, int* waiting) {
         // 2. check_every batched steps of every live slot
         SRV_CUDA(cudaGraphLaunch(s->gexec, s->stream));
         // 3. per-slot FP64 diagnostics
-        const float inv = (float)(1.0 / s->scale);
         const int tiles = s->htab->total_tiles;
-        switch (s->storage) {
-            case HLBM_F32: k_batched_partials<StoreF32><<<tiles, dim3(kTileX, kTileY), 0, s->stream>>>(s->dtab, inv, s->dpartials); break;
-            case HLBM_F16DEV: k_batched_partials<StoreF16><<<tiles, dim3(kTileX, kTileY), 0, s->stream>>>(s->dtab, inv, s->dpartials); break;
-            default: k_batched_partials<StoreBF16><<<tiles, dim3(kTileX, kTileY), 0, s->stream>>>(s->dtab, inv, s->dpartials); break;
-        }
+        k_batched_partials<<<tiles, dim3(kTileX, kTileY), 0, s->stream>>>(s->dtab, s->dpartials);
         SRV_CUDA(cudaGetLastError());
         const int ns = (int)s->live.size();
         k_batched_final<<<ns, 256, 0, s->stream>>>(s->dtab, s->dpartials, s->dout);
@@ -615,18 +695,35 @@ int hlbm_server_pump(hlbm_server_t* s, int* active, int* waiting) {
         SRV_CUDA(cudaMemcpyAsync(s->hout, s->dout, (size_t)ns * 8 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
         SRV_CUDA(cudaStreamSynchronize(s->stream));
         s->rounds++;
-        // 4. retire converged / exhausted / cancelled slots
+        // 4. retire converged / exhausted / cancelled slots; widen slots at their floor
         std::vector<Live> keep;
         keep.reserve(s->live.size());
         for (int k = 0; k < ns; ++k) {
             Live& l = s->live[k];
             l.steps += s->check_every;
+            if (l.ds.storage != HLBM_F32) l.steps_low += s->check_every;
             s->lups += (long long)s->check_every * l.ds.nx * l.ds.ny * l.ds.nz;
             const double* o = s->hout + (size_t)k * 8;
+            const bool low = l.ds.storage != HLBM_F32;
             int status = 1;
             if (l.cancel) status = HLBM_ERR_CANCELLED;
-            else if (o[6] < l.p.req.tol) status = HLBM_OK;
+            else if (o[6] < l.p.req.tol && !(low && s->refine)) status = HLBM_OK;
             else if (l.steps >= l.p.req.max_steps) status = HLBM_ERR_NOT_CONVERGED;
+            if (status == 1 && low && s->refine) {
+                if (o[6] < 0.9 * l.best_du) {
+                    l.best_du = o[6];
+                    l.stall = 0;
+                } else {
+                    ++l.stall;
+                }
+                const bool at_floor = o[6] < std::max(l.p.req.tol, s->floor_coef * o[7]) || l.stall >= kStallChecks;
+                if (at_floor) {
+                    cudaError_t e = widen_to_fp32(s, l);
+                    if (e == cudaErrorMemoryAllocation) cudaGetLastError();  // retry at a later round
+                    else if (e != cudaSuccess) return srv_cuda_fail(e);
+                    else s->table_dirty = true;
+                }
+            }
             if (status == 1) {
                 keep.push_back(l);
                 continue;

@@ -16,13 +16,19 @@ import numpy as np
 
 from . import (HLBM_F16DEV, HLBM_F32, HLBM_D3Q19, HLBM_TWO_LATTICE, Lattice, hlbm_request,
                hlbm_server_cancel, hlbm_server_create, hlbm_server_destroy, hlbm_server_info,
-               hlbm_server_inject_alloc_failures, hlbm_server_poll, hlbm_server_pump, hlbm_server_submit)
+               hlbm_server_inject_alloc_failures, hlbm_server_poll, hlbm_server_pump, hlbm_server_set_refinement,
+               hlbm_server_submit)
 
 
 class Server:
-    def __init__(self, mem_budget=32 << 30, storage=HLBM_F16DEV, check_every=100, stream=None):
+    def __init__(self, mem_budget=32 << 30, storage=HLBM_F16DEV, check_every=100, stream=None, refine=None,
+                 floor_coef=None):
         self.s = hlbm_server_create(mem_budget, storage, check_every, stream)
         self._keep = {}  # id -> (field, u_out) kept alive until polled
+        if refine is not None or floor_coef is not None:
+            default = 1.6e-2 if storage == 3 else 2e-3
+            hlbm_server_set_refinement(self.s, True if refine is None else refine,
+                                       default if floor_coef is None else floor_coef)
 
     def close(self):
         if self.s:

@@ -170,3 +170,29 @@ def test_converges_to_steady_state():
     st = lat.reduce()
     lat.close()
     assert abs(r["k_app"] - st["k_app"]) / st["k_app"] < 1e-2
+
+
+def test_precision_ladder_reaches_tolerance():
+    """A fast flow (period 64, r = 0.3 P: max|u| ~ 1e-2) cannot reach max|du| < 1e-6 in FP16
+    storage (its rounding floor is ~6e-4 max|u|). With refinement the slot moves to FP32 at
+    the floor and converges; its permeability agrees with an FP32-only server within 1 %."""
+    vp = field(64, 64, 0.3)
+    kw = dict(tau=0.6, F=(1e-6, 0, 0), tol=1e-6, max_steps=200000)
+    srv = Server(4 << 30, hb.HLBM_F16DEV, 100)
+    srv.submit(vp, **kw)
+    (r,) = srv.run_until_idle()
+    srv.close()
+    assert r["status"] == hb.HLBM_OK, r
+    assert r["final_storage"] == hb.HLBM_F32 and 0 < r["steps_low"] < r["steps"]
+    ref_srv = Server(4 << 30, hb.HLBM_F32, 100)
+    ref_srv.submit(vp, **kw)
+    (ref,) = ref_srv.run_until_idle()
+    ref_srv.close()
+    assert ref["status"] == hb.HLBM_OK and ref["steps_low"] == 0
+    assert abs(r["k_app"] - ref["k_app"]) / ref["k_app"] < 1e-2
+    # without refinement the FP16 slot stalls above the tolerance
+    off = Server(4 << 30, hb.HLBM_F16DEV, 100, refine=False)
+    off.submit(vp, tau=0.6, F=(1e-6, 0, 0), tol=1e-6, max_steps=20000)
+    (o,) = off.run_until_idle()
+    off.close()
+    assert o["status"] == hb.HLBM_ERR_NOT_CONVERGED and o["final_storage"] == hb.HLBM_F16DEV
