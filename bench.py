@@ -229,6 +229,39 @@ def run_reference(args, w, rank):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def adjoint_leg(n=128, nsteps=2000, every=45, period=32, ratio=0.3, tau=0.6, F=(1e-6, 0.0, 0.0)):
+    """Gradient of the outflow flux w.r.t. varpi on the adjoint workload (128^3 regular spheres,
+    2000 steps, state kept every 45 steps): wall time of the whole call and its algorithmic
+    bytes (forward run + segment recomputation at 156 B/LUP, reverse steps at 240 B/LUP)."""
+    import torch
+    import paper_2310_14746_gb300 as hb
+    from paper_2310_14746_gb300 import inputs
+    vp = inputs.regular_sphere_field(n, period=period, radius_ratio=ratio)
+    lat = hb.Lattice(19, n, n, n, hb.HLBM_F32, hb.HLBM_TWO_LATTICE)
+    lat.set_relaxation(tau)
+    lat.set_force(*F)
+    lat.set_porosity(vp)
+    grad = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    lat.init_equilibrium()
+    lat.adjoint_flux_grad(2 * every, every, n - 1, grad)  # warm-up (allocator, modules)
+    lat.init_equilibrium()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, _ = lat.adjoint_flux_grad(nsteps, every, n - 1, grad)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    lat.close()
+    cells = n ** 3
+    nsnap = (nsteps - 1) // every + 1
+    algo = cells * ((2 * nsteps - nsnap) * 156 + nsteps * 240)
+    peak, kind = measured_hbm_peak()
+    return {"workload": "D3Q19 %d^3 regular spheres (period %d, r = %.1f P), %d steps, checkpoint every %d"
+                        % (n, period, ratio, nsteps, every),
+            "seconds": dt, "J": J, "adjoint_mlups": cells * nsteps / dt / 1e6,
+            "achieved_GBps": algo / dt / 1e9, "frac_of_peak": algo / dt / 1e9 / peak, "peak_kind": kind,
+            "grad_abs_max": float(grad.abs().max().item())}
+
+
 def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, world=1, dist=None):
     """Serving stream sample: the first n_requests of the seeded trace (edges up to max_edge).
     1) capacity: all requests at t = 0 through the batched FP16 server -> solves/s;
@@ -375,6 +408,10 @@ def run_gpu(args, w, rank, world, local_rank):
     kname = "stream_collide_d%dq%d_%s_%s" % (3 if q == 19 else 2, q, w["storage"], w["pattern"])
     traffic = KERNEL_TRAFFIC_BYTES.get((kname, n))
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = adjoint_leg()
+
     serving = None
     if args.serving_requests > 0:
         lat.close()
@@ -404,6 +441,7 @@ def run_gpu(args, w, rank, world, local_rank):
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "stats": {"k_app": st["k_app"], "mass_rel_drift": st["mass"] / cells - 1.0, "max_du": st["max_du"]},
+            "adjoint": adjoint,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
@@ -423,9 +461,10 @@ def main():
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=0,
-                    help="also replay this many requests of the seeded serving trace (batched vs plain)")
-    ap.add_argument("--serving-max-edge", type=int, default=192)
+    ap.add_argument("--serving-requests", type=int, default=16,
+                    help="replay this many requests of the seeded serving trace, batched vs plain (0: skip)")
+    ap.add_argument("--serving-max-edge", type=int, default=128)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient leg")
     args = ap.parse_args()
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)

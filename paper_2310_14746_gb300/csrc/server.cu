@@ -43,17 +43,20 @@ namespace hlbm {
 namespace srv {
 
 constexpr int kMaxSlots = 1024;
-constexpr int kTileX = 32, kTileY = 8;
+constexpr int kBlock = 256;  // threads per block; a tile is tw x (256 / tw) cells of one slot
 
 struct DevSlot {
     void* f[2];
     float* varpi;
     float* u_prev;
     int nx, ny, nz;
+    int tw_log2;  // tile width in x is 2^tw_log2 = min(128, nx rounded up to a power of two >= 32)
     int tiles_x, tiles_y;
+    float rcp_tiles_x, rcp_tiles_y;  // 1/tiles_x, 1/tiles_y for the quotient estimate
     int tile_begin;
     int ntiles;
     int storage;  // HLBM_F32, HLBM_F16DEV or HLBM_BF16DEV
+    int fx_only;  // body force along x only
     float scale, inv_scale;
     Phys<float> ph;
     double nu, Fx64;
@@ -62,7 +65,7 @@ struct DevSlot {
 struct DevTable {
     int nslots;
     int total_tiles;
-    int pad[2];
+    int lo[4], hi[4];  // tile range of the slots in each storage (indexed by HLBM_F64..HLBM_BF16DEV)
     DevSlot slot[kMaxSlots];
 };
 
@@ -91,30 +94,57 @@ __device__ __forceinline__ void advance_cell(const DevSlot& sl, int k, int x, in
     C d[19];
 #pragma unroll
     for (int i = 0; i < 19; ++i) d[i] = S::load_raw(fin, gather_index<19, false>(g, nb, cell, i, NATURAL));
-    collide<19, C, S::scaled>(d, C(__ldg(sl.varpi + cell)), ph, C(sl.scale), C(sl.inv_scale));
+    const C vp = C(__ldg(sl.varpi + cell));
+    if (sl.fx_only) collide<19, C, S::scaled, true>(d, vp, ph, C(sl.scale), C(sl.inv_scale));
+    else collide<19, C, S::scaled, false>(d, vp, ph, C(sl.scale), C(sl.inv_scale));
 #pragma unroll
     for (int i = 0; i < 19; ++i) S::store_raw(fout, i * (int)g.N + cell, d[i]);
 }
 
-__global__ void __launch_bounds__(kTileX * kTileY) k_batched_step(const DevTable* __restrict__ tab, int k) {
-    const int total = tab->total_tiles;
-    const int ns = tab->nslots;
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        const DevSlot& sl = tab->slot[find_slot(tab, t, ns)];
-        const int lt = t - sl.tile_begin;
-        const int tx = lt % sl.tiles_x;
-        const int rest = lt / sl.tiles_x;
-        const int ty = rest % sl.tiles_y;
-        const int z = rest / sl.tiles_y;
-        const int x = tx * kTileX + threadIdx.x;
-        const int y = ty * kTileY + threadIdx.y;
-        if (x >= sl.nx || y >= sl.ny) continue;
-        switch (sl.storage) {
-            case HLBM_F16DEV: advance_cell<StoreF16>(sl, k, x, y, z); break;
-            case HLBM_BF16DEV: advance_cell<StoreBF16>(sl, k, x, y, z); break;
-            default: advance_cell<StoreF32>(sl, k, x, y, z); break;
-        }
+// q = n / d and r = n % d for 0 <= n < 2^21, d >= 1 (a slot has fewer tiles): a float-reciprocal
+// estimate corrected to the exact quotient (no integer division; checked
+// exhaustively on the host for n < 2^21 and d up to 256 plus larger samples).
+__device__ __forceinline__ int divmod(int n, int d, float rcp, int& r) {
+    int q = __float2int_rz(__int2float_rn(n) * rcp);
+    r = n - q * d;
+    if (r < 0) {
+        --q;
+        r += d;
+    } else if (r >= d) {
+        ++q;
+        r -= d;
     }
+    return q;
+}
+
+// Cell of thread `tid` in tile `lt` of a slot (x, y, z); false past the lattice edge.
+__device__ __forceinline__ bool tile_cell(const DevSlot& sl, int lt, int tid, int& x, int& y, int& z) {
+    int tx, ty;
+    const int rest = divmod(lt, sl.tiles_x, sl.rcp_tiles_x, tx);
+    z = divmod(rest, sl.tiles_y, sl.rcp_tiles_y, ty);
+    const int tw = 1 << sl.tw_log2;
+    x = tx * tw + (tid & (tw - 1));
+    y = ty * (kBlock >> sl.tw_log2) + (tid >> sl.tw_log2);
+    return x < sl.nx && y < sl.ny;
+}
+
+// One time step of one tile of a live slot stored as S: block b handles tile
+// lo[S] + b of the table (the slots of each storage form one contiguous tile
+// range, so each storage has its own kernel and registers); blocks past the
+// range exit at once. The tile's slot descriptor is staged in shared memory,
+// so its fields are read where they are used instead of held in registers.
+template <class S>
+__global__ void __launch_bounds__(kBlock, 4) k_batched_step(const DevTable* __restrict__ tab, int k) {
+    __shared__ DevSlot sl;
+    constexpr int kWords = (int)(sizeof(DevSlot) / sizeof(int));
+    const int t = tab->lo[S::kind] + blockIdx.x;
+    if (t >= tab->hi[S::kind]) return;  // uniform over the block
+    if ((int)threadIdx.x < kWords)
+        reinterpret_cast<int*>(&sl)[threadIdx.x] =
+            reinterpret_cast<const int*>(&tab->slot[find_slot(tab, t, tab->nslots)])[threadIdx.x];
+    __syncthreads();
+    int x, y, z;
+    if (tile_cell(sl, t - sl.tile_begin, threadIdx.x, x, y, z)) advance_cell<S>(sl, k, x, y, z);
 }
 
 __device__ __forceinline__ double wsum(double v) {
@@ -164,27 +194,21 @@ __device__ __forceinline__ void cell_stats(const DevSlot& sl, int x, int y, int 
 
 // Per-tile FP64 partials of the diagnostics (one block per tile of any slot):
 // sum drho, sum rho*u (3), plane flux, -, max|du|, max|u|.
-__global__ void __launch_bounds__(kTileX * kTileY)
+__global__ void __launch_bounds__(kBlock)
 k_batched_partials(const DevTable* __restrict__ tab, double* __restrict__ partials) {
     __shared__ double sh[8][8];
     const int t = blockIdx.x;
     const DevSlot& sl = tab->slot[find_slot(tab, t, tab->nslots)];
-    const int lt = t - sl.tile_begin;
-    const int tx = lt % sl.tiles_x;
-    const int rest = lt / sl.tiles_x;
-    const int ty = rest % sl.tiles_y;
-    const int z = rest / sl.tiles_y;
-    const int x = tx * kTileX + threadIdx.x;
-    const int y = ty * kTileY + threadIdx.y;
+    int x, y, z;
     double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (x < sl.nx && y < sl.ny) {
+    if (tile_cell(sl, t - sl.tile_begin, threadIdx.x, x, y, z)) {
         switch (sl.storage) {
             case HLBM_F16DEV: cell_stats<StoreF16>(sl, x, y, z, v); break;
             case HLBM_BF16DEV: cell_stats<StoreBF16>(sl, x, y, z, v); break;
             default: cell_stats<StoreF32>(sl, x, y, z, v); break;
         }
     }
-    const int tid = threadIdx.x + kTileX * threadIdx.y;
+    const int tid = threadIdx.x;
 #pragma unroll
     for (int c = 0; c < 8; ++c) v[c] = c >= 6 ? wmax(v[c]) : wsum(v[c]);
     if ((tid & 31) == 0)
@@ -315,7 +339,7 @@ struct hlbm_server {
     DevTable* htab = nullptr;
     bool table_dirty = true;
     cudaGraphExec_t gexec = nullptr;
-    int grid = 0;
+    int grid_low = 0, grid_f32 = 0;  // blocks of the captured launches (>= the tiles they cover)
     double* dpartials = nullptr;
     size_t partial_cap = 0;  // tiles
     double* dout = nullptr;
@@ -436,9 +460,15 @@ cudaError_t admit(hlbm_server_t* s, Pending& p, Live& l) {
     l.ds.nx = r.nx;
     l.ds.ny = r.ny;
     l.ds.nz = r.nz;
-    l.ds.tiles_x = (r.nx + kTileX - 1) / kTileX;
-    l.ds.tiles_y = (r.ny + kTileY - 1) / kTileY;
+    l.ds.tw_log2 = 5;
+    while (l.ds.tw_log2 < 7 && (1 << l.ds.tw_log2) < r.nx) ++l.ds.tw_log2;
+    const int tw = 1 << l.ds.tw_log2, th = kBlock / tw;
+    l.ds.tiles_x = (r.nx + tw - 1) / tw;
+    l.ds.tiles_y = (r.ny + th - 1) / th;
+    l.ds.rcp_tiles_x = 1.0f / (float)l.ds.tiles_x;
+    l.ds.rcp_tiles_y = 1.0f / (float)l.ds.tiles_y;
     l.ds.ntiles = l.ds.tiles_x * l.ds.tiles_y * r.nz;
+    l.ds.fx_only = r.F[1] == 0.0 && r.F[2] == 0.0;
     l.ds.storage = s->storage;
     l.ds.scale = (float)scale_of(s->storage);
     l.ds.inv_scale = (float)(1.0 / scale_of(s->storage));
@@ -500,30 +530,54 @@ cudaError_t widen_to_fp32(hlbm_server_t* s, Live& l) {
     return cudaSuccess;
 }
 
+// Capture check_every steps (per step: the reduced-precision slots' kernel, then
+// the FP32 slots' kernel) with the current grid sizes.
 int build_graph(hlbm_server_t* s) {
     if (!s->cap_stream) SRV_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
-    int per_sm = 0, sms = 0;
-    SRV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_step, kTileX * kTileY, 0));
-    SRV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
-    s->grid = std::max(1, per_sm) * sms;
     cudaGraph_t graph = nullptr;
     SRV_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < s->check_every; ++k)
-        k_batched_step<<<s->grid, dim3(kTileX, kTileY), 0, s->cap_stream>>>(s->dtab, k);
+    for (int k = 0; k < s->check_every; ++k) {
+        if (s->grid_low > 0 && s->storage == HLBM_F16DEV)
+            k_batched_step<StoreF16><<<s->grid_low, kBlock, 0, s->cap_stream>>>(s->dtab, k);
+        if (s->grid_low > 0 && s->storage == HLBM_BF16DEV)
+            k_batched_step<StoreBF16><<<s->grid_low, kBlock, 0, s->cap_stream>>>(s->dtab, k);
+        if (s->grid_f32 > 0) k_batched_step<StoreF32><<<s->grid_f32, kBlock, 0, s->cap_stream>>>(s->dtab, k);
+    }
     cudaError_t e = cudaStreamEndCapture(s->cap_stream, &graph);
     if (e != cudaSuccess) return srv_cuda_fail(e);
+    if (s->gexec) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
     e = cudaGraphInstantiate(&s->gexec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return srv_cuda_fail(e);
     return HLBM_OK;
 }
 
+// Grid for `tiles` tiles: a power of two >= tiles, kept while it stays within 8x.
+int fit_grid(int cur, int tiles) {
+    if (tiles == 0) return cur;
+    if (cur >= tiles && cur <= 8 * tiles) return cur;
+    int g = 256;
+    while (g < tiles) g *= 2;
+    return g;
+}
+
 int upload_table(hlbm_server_t* s) {
+    // slots grouped by storage (each storage kernel strides over its own range);
+    // a slot's arithmetic does not depend on its position in the table
+    std::stable_sort(s->live.begin(), s->live.end(),
+                     [](const Live& a, const Live& b) { return a.ds.storage < b.ds.storage; });
     int tiles = 0;
     s->htab->nslots = (int)s->live.size();
+    for (int st = 0; st < 4; ++st) s->htab->lo[st] = s->htab->hi[st] = 0;
     for (size_t k = 0; k < s->live.size(); ++k) {
+        const int st = s->live[k].ds.storage;
+        if (k == 0 || s->live[k - 1].ds.storage != st) s->htab->lo[st] = tiles;
         s->live[k].ds.tile_begin = tiles;
         tiles += s->live[k].ds.ntiles;
+        s->htab->hi[st] = tiles;
         s->htab->slot[k] = s->live[k].ds;
     }
     s->htab->total_tiles = tiles;
@@ -538,6 +592,14 @@ int upload_table(hlbm_server_t* s) {
     const size_t bytes = offsetof(DevTable, slot) + sizeof(DevSlot) * s->live.size();
     SRV_CUDA(cudaMemcpyAsync(s->dtab, s->htab, bytes, cudaMemcpyHostToDevice, s->stream));
     s->table_dirty = false;
+    const int low = s->storage == HLBM_F32 ? 0 : s->htab->hi[s->storage] - s->htab->lo[s->storage];
+    const int f32 = s->htab->hi[HLBM_F32] - s->htab->lo[HLBM_F32];
+    const int gl = fit_grid(s->grid_low, low), gf = fit_grid(s->grid_f32, f32);
+    if (gl != s->grid_low || gf != s->grid_f32 || !s->gexec) {
+        s->grid_low = gl;
+        s->grid_f32 = gf;
+        return build_graph(s);
+    }
     return HLBM_OK;
 }
 
@@ -571,8 +633,8 @@ int hlbm_server_create(hlbm_server_t** out, size_t mem_budget, int storage, int 
         std::memset(s->htab, 0, sizeof(DevTable));
         e = cudaMemcpy(s->dtab, s->htab, sizeof(DevTable), cudaMemcpyHostToDevice);
     }
-    int rc = e == cudaSuccess ? build_graph(s) : srv_cuda_fail(e);
-    if (rc != HLBM_OK) {
+    if (e != cudaSuccess) {
+        int rc = srv_cuda_fail(e);
         hlbm_server_destroy(s);
         return rc;
     }
@@ -687,7 +749,7 @@ int hlbm_server_pump(hlbm_server_t* s, int* active, int* waiting) {
         SRV_CUDA(cudaGraphLaunch(s->gexec, s->stream));
         // 3. per-slot FP64 diagnostics
         const int tiles = s->htab->total_tiles;
-        k_batched_partials<<<tiles, dim3(kTileX, kTileY), 0, s->stream>>>(s->dtab, s->dpartials);
+        k_batched_partials<<<tiles, kBlock, 0, s->stream>>>(s->dtab, s->dpartials);
         SRV_CUDA(cudaGetLastError());
         const int ns = (int)s->live.size();
         k_batched_final<<<ns, 256, 0, s->stream>>>(s->dtab, s->dpartials, s->dout);
