@@ -85,6 +85,9 @@ extern "C" {
 #define HLBM_PERIODIC 0
 #define HLBM_HALFWAY_BOUNCE_BACK 1 /* walls half a cell outside both ends  */
 
+#define HLBM_HOMOG_SHIFT 0 /* equilibrium at varpi*u (eq. porousVeloMaxwellian) */
+#define HLBM_HOMOG_DRAG 1  /* equilibrium at u, drag -lam rho u in the force  */
+
 typedef struct hlbm_lattice hlbm_t;
 
 /* FP64 diagnostics of the current state (see hlbm_reduce). */
@@ -128,6 +131,29 @@ int hlbm_set_relaxation(hlbm_t* h, double tau);
  * (synchronises). varpi = 1 is plain BGK, varpi = 0 a solid cell. */
 int hlbm_set_porosity(hlbm_t* h, const float* varpi, int on_device);
 
+/* Resolved obstacles: nx*ny*nz bytes, nonzero = solid cell (copied; host or
+ * device). A fluid cell whose pull source is solid takes the bounce-back
+ * population of its opposite direction (no slip half-way on the solid
+ * surface); solid cells are not updated and report rho = 1, u = 0 (and rest
+ * populations from hlbm_get_populations). With varpi = 1 in the fluid this is
+ * the pore-scale problem whose permeability the homogenized field stands in
+ * for (Thm. thmStatNSECase4). NULL removes the obstacles. Set the domain
+ * boundaries first (hlbm_set_boundary returns HLBM_ERR_STATE while a mask is
+ * set); the post-collision state of the fluid cells is kept across the call.
+ * Not supported by hlbm_adjoint_flux_grad (HLBM_ERR_STATE). Synchronises. */
+int hlbm_set_solid_mask(hlbm_t* h, const unsigned char* solid, int on_device);
+
+/* Anisotropic porosity control: a diagonal tensor per cell, 3*nx*ny*nz FP32
+ * values [3][z][y][x] (varpi_x, varpi_y, varpi_z), each in [0, 1]; copied and
+ * validated like hlbm_set_porosity. The Maxwellian is then evaluated at
+ * (varpi_x u_x, varpi_y u_y, varpi_z u_z): a drag nu/K_a per axis with
+ * varpi_a = 1 - nu tau / K_a, beyond the isotropy assumption of Sec. 2.5
+ * (Assumption thmAssump, item 3). A later hlbm_set_porosity returns to the
+ * isotropic field. Shift form only (HLBM_ERR_STATE with the drag form);
+ * hlbm_adjoint_flux_grad needs the isotropic field. Costs 8 more bytes per
+ * cell update. */
+int hlbm_set_porosity_tensor(hlbm_t* h, const float* varpi3, int on_device);
+
 /* varpi = 1 - nu*tau/K for n host values (eq. "d definition"), clamped to
  * [0, 1]; K <= 0 or NaN gives 0, K = +inf gives 1. Pure host function. */
 int hlbm_porosity_from_permeability(const float* K, double nu, double tau, float* varpi,
@@ -139,6 +165,17 @@ int hlbm_set_force(hlbm_t* h, double Fx, double Fy, double Fz);
 /* Boundary type of axis 0 (x), 1 (y) or 2 (z): HLBM_PERIODIC or
  * HLBM_HALFWAY_BOUNCE_BACK (no-slip u = 0 on the boundary, eq. targetEBTL). */
 int hlbm_set_boundary(hlbm_t* h, int axis, int type);
+
+/* Form of the homogenization term. HLBM_HOMOG_SHIFT (default) evaluates the
+ * Maxwellian at varpi*u (Sec. 3.2, eq. porousVeloMaxwellian). HLBM_HOMOG_DRAG
+ * uses the equivalent drag of Sec. 3.3 (eq. momentumHLBM: the shift acts as
+ * -nu K^{-1} rho u): the equilibrium stays at u and the force becomes
+ * G = F - lam rho u with lam = nu/K = (1 - varpi)/tau, u being the half-force
+ * velocity of the total force, u = (j + F/2) / (rho (1 + lam/2)); hlbm_moments
+ * and hlbm_reduce then report that u. Both forms give Darcy's u = F K / nu at
+ * uniform porosity. hlbm_adjoint_flux_grad supports the shift form only
+ * (HLBM_ERR_STATE otherwise). */
+int hlbm_set_homogenization(hlbm_t* h, int form);
 
 /* Storage scale s of the FP16 deviation policy (a power of two in
  * [1, 2^20]); other policies accept only 1. Applies to later writes of

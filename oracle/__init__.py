@@ -46,6 +46,14 @@ def _load():
         lib.oracle_flux.argtypes = [i, i, i, i, _ip, _dp, _dp, _dp]
         lib.oracle_flux_grad.argtypes = [i, i, i, i, _ip, d, _dp, _dp, _dp, L, i, _dp, _dp]
         lib.oracle_porosity_from_permeability.argtypes = [_dp, d, d, _dp, ctypes.c_int64]
+        lib.oracle_collide_mode.argtypes = [i, _dp, d, d, _dp, i, _dp]
+        lib.oracle_run_mode.argtypes = [i, i, i, i, _ip, d, _dp, _dp, _dp, _dp, L, i]
+        lib.oracle_moments_mode.argtypes = [i, i, i, i, _ip, d, _dp, _dp, _dp, i, _dp, _dp]
+        lib.oracle_run_aniso.argtypes = [i, i, i, i, _ip, d, _dp, _dp, _dp, _dp, L]
+        lib.oracle_collide_aniso.argtypes = [i, _dp, _dp, d, _dp, _dp]
+        _up = ctypes.POINTER(ctypes.c_ubyte)
+        lib.oracle_run_masked.argtypes = [i, i, i, i, _ip, d, _dp, _dp, _up, _dp, _dp, L]
+        lib.oracle_moments_masked.argtypes = [i, i, i, i, _ip, _dp, _up, _dp, _dp, _dp]
         _lib = lib
     return _lib
 
@@ -228,6 +236,118 @@ def flux_grad(f0, varpi, tau, F, bc, nsteps, every=45):
     if rc:
         raise RuntimeError("oracle_flux_grad failed (%d)" % rc)
     return J.value, grad
+
+
+SHIFT, DRAG = 0, 1  # homogenization forms: equilibrium shift (eq. porousVeloMaxwellian), explicit drag
+
+
+def collide_mode(q, g, varpi, tau, F, mode):
+    """One cell's collision in the given homogenization form."""
+    lib = _load()
+    g = _f64(g)
+    FF = _f64(np.asarray(F, dtype=np.float64).reshape(3))
+    out = np.zeros(q)
+    if lib.oracle_collide_mode(q, _p(g), float(varpi), float(tau), _p(FF), int(mode), _p(out)):
+        raise ValueError("bad mode or q")
+    return out
+
+
+def run_mode(f, varpi, tau, F, bc, nsteps, mode):
+    """oracle.run in the given homogenization form."""
+    lib = _load()
+    f = _f64(f).copy()
+    q = f.shape[0]
+    nx, ny, nz = _dims(f.shape[1:])
+    vp = _f64(varpi)
+    FF = _f64(np.asarray(F, dtype=np.float64).reshape(3))
+    b = _bc(bc)
+    tmp = np.empty_like(f)
+    if lib.oracle_run_mode(q, nx, ny, nz, b.ctypes.data_as(_ip), float(tau), _p(FF), _p(vp), _p(f), _p(tmp),
+                           int(nsteps), int(mode)):
+        raise ValueError("oracle_run_mode rejected its arguments")
+    return f
+
+
+def moments_mode(f, varpi, tau, F, bc, mode):
+    """(rho, u) of a state as the collision of the given form sees them."""
+    lib = _load()
+    f = _f64(f)
+    q = f.shape[0]
+    nx, ny, nz = _dims(f.shape[1:])
+    vp = _f64(varpi)
+    FF = _f64(np.asarray(F, dtype=np.float64).reshape(3))
+    b = _bc(bc)
+    rho = np.empty(f.shape[1:])
+    u = np.empty((3,) + f.shape[1:])
+    lib.oracle_moments_mode(q, nx, ny, nz, b.ctypes.data_as(_ip), float(tau), _p(FF), _p(vp), _p(f), int(mode),
+                            _p(rho), _p(u))
+    return rho, u
+
+
+def collide_aniso(q, g, varpi3, tau, F):
+    """One cell's collision with a diagonal porosity tensor (varpi_x, varpi_y, varpi_z)."""
+    lib = _load()
+    g = _f64(g)
+    v3 = _f64(np.asarray(varpi3, dtype=np.float64).reshape(3))
+    FF = _f64(np.asarray(F, dtype=np.float64).reshape(3))
+    out = np.zeros(q)
+    lib.oracle_collide_aniso(q, _p(g), _p(v3), float(tau), _p(FF), _p(out))
+    return out
+
+
+def run_aniso(f, varpi3, tau, F, bc, nsteps):
+    """oracle.run with a per-cell diagonal porosity tensor varpi3[3][z][y][x]."""
+    lib = _load()
+    f = _f64(f).copy()
+    q = f.shape[0]
+    nx, ny, nz = _dims(f.shape[1:])
+    v3 = _f64(varpi3)
+    assert v3.shape == (3,) + f.shape[1:]
+    FF = _f64(np.asarray(F, dtype=np.float64).reshape(3))
+    b = _bc(bc)
+    tmp = np.empty_like(f)
+    if lib.oracle_run_aniso(q, nx, ny, nz, b.ctypes.data_as(_ip), float(tau), _p(FF), _p(v3), _p(f), _p(tmp),
+                            int(nsteps)):
+        raise ValueError("oracle_run_aniso rejected its arguments")
+    return f
+
+
+def _u8(a):
+    return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def run_masked(f, varpi, solid, tau, F, bc, nsteps):
+    """oracle.run with resolved solid cells (bounce-back on their surfaces)."""
+    lib = _load()
+    f = _f64(f).copy()
+    q = f.shape[0]
+    nx, ny, nz = _dims(f.shape[1:])
+    vp = _f64(varpi)
+    so = _u8(solid)
+    assert so.shape == f.shape[1:]
+    FF = _f64(np.asarray(F, dtype=np.float64).reshape(3))
+    b = _bc(bc)
+    tmp = np.empty_like(f)
+    if lib.oracle_run_masked(q, nx, ny, nz, b.ctypes.data_as(_ip), float(tau), _p(FF), _p(vp),
+                             so.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), _p(f), _p(tmp), int(nsteps)):
+        raise ValueError("oracle_run_masked rejected its arguments")
+    return f
+
+
+def moments_masked(f, solid, F, bc):
+    """(rho, u) with solid cells reported as rho = 1, u = 0."""
+    lib = _load()
+    f = _f64(f)
+    q = f.shape[0]
+    nx, ny, nz = _dims(f.shape[1:])
+    so = _u8(solid)
+    FF = _f64(np.asarray(F, dtype=np.float64).reshape(3))
+    b = _bc(bc)
+    rho = np.empty(f.shape[1:])
+    u = np.empty((3,) + f.shape[1:])
+    lib.oracle_moments_masked(q, nx, ny, nz, b.ctypes.data_as(_ip), _p(FF),
+                              so.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)), _p(f), _p(rho), _p(u))
+    return rho, u
 
 
 def equilibrium_state(q, shape, rho0=1.0, u0=(0.0, 0.0, 0.0)):

@@ -149,6 +149,77 @@ static void or_collide_cell(const or_velset* vs, const double* g, double varpi, 
     }
 }
 
+/* The explicit-drag form of the homogenization (Sec. 3.3, eq. momentumHLBM:
+ * the equilibrium shift acts as the drag -nu K^{-1} rho u, and with
+ * varpi = 1 - nu tau/K, nu/K = (1 - varpi)/tau =: lam). The equilibrium stays
+ * at the velocity u and the drag joins the body force, G = F - lam rho u, in
+ * Guo's scheme; u is the half-force velocity of the total force, which is
+ * implicit in u: rho u = j + G/2 = j + F/2 - lam rho u / 2, so
+ * u = (j + F/2) / (rho (1 + lam/2)). */
+static void or_collide_cell_drag(const or_velset* vs, const double* g, double varpi, double tau,
+                                 const double F[3], double* out)
+{
+    int i, d;
+    double rho = 0.0, j[3] = {0.0, 0.0, 0.0}, u[3], G[3], feq[OR_MAXQ];
+    const double lam = (1.0 - varpi) / tau;
+    for (i = 0; i < vs->q; ++i) {
+        rho += g[i];
+        for (d = 0; d < 3; ++d) j[d] += vs->c[i][d] * g[i];
+    }
+    for (d = 0; d < 3; ++d) {
+        u[d] = (j[d] + 0.5 * F[d]) / (rho * (1.0 + 0.5 * lam));
+        G[d] = F[d] - lam * rho * u[d];
+    }
+    or_equilibrium(vs, rho, u, feq);
+    for (i = 0; i < vs->q; ++i) {
+        const int* c = vs->c[i];
+        double cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+        double cG = c[0] * G[0] + c[1] * G[1] + c[2] * G[2];
+        double cmuG = (c[0] - u[0]) * G[0] + (c[1] - u[1]) * G[1] + (c[2] - u[2]) * G[2];
+        double S = (1.0 - 0.5 / tau) * vs->w[i] * (3.0 * cmuG + 9.0 * cu * cG);
+        out[i] = g[i] - (g[i] - feq[i]) / tau + S;
+    }
+}
+
+/* Anisotropic (diagonal-tensor) porosity control, beyond the isotropy assumption
+ * of Sec. 2.5 (Assumption thmAssump, item 3) and listed as future work in the
+ * outlook: the Maxwellian is evaluated at v = (varpi_x u_x, varpi_y u_y,
+ * varpi_z u_z), i.e. a drag -nu K_a^{-1} rho u_a per axis with
+ * varpi_a = 1 - nu tau / K_a. Otherwise as or_collide_cell. */
+static void or_collide_cell_aniso(const or_velset* vs, const double* g, const double varpi[3], double tau,
+                                  const double F[3], double* out)
+{
+    int i;
+    double rho, u[3], v[3], feq[OR_MAXQ];
+    or_moments_cell(vs, g, F, &rho, u);
+    v[0] = varpi[0] * u[0];
+    v[1] = varpi[1] * u[1];
+    v[2] = varpi[2] * u[2];
+    or_equilibrium(vs, rho, v, feq);
+    for (i = 0; i < vs->q; ++i) {
+        const int* c = vs->c[i];
+        double cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+        double cF = c[0] * F[0] + c[1] * F[1] + c[2] * F[2];
+        double cmuF = (c[0] - u[0]) * F[0] + (c[1] - u[1]) * F[1] + (c[2] - u[2]) * F[2];
+        double S = (1.0 - 0.5 / tau) * vs->w[i] * (3.0 * cmuF + 9.0 * cu * cF);
+        out[i] = g[i] - (g[i] - feq[i]) / tau + S;
+    }
+}
+
+/* Velocity of the streamed populations g as the collision of `mode` sees it
+ * (0: equilibrium shift, half-force velocity of F; 1: explicit drag, half-force
+ * velocity of F + drag). */
+static void or_velocity_mode(const or_velset* vs, const double* g, double varpi, double tau,
+                             const double F[3], int mode, double* rho_out, double u[3])
+{
+    int d;
+    or_moments_cell(vs, g, F, rho_out, u);
+    if (mode == 1) {
+        const double lam = (1.0 - varpi) / tau;
+        for (d = 0; d < 3; ++d) u[d] /= (1.0 + 0.5 * lam);
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Streaming                                                                  */
 /* ------------------------------------------------------------------------ */
@@ -249,6 +320,220 @@ int oracle_stream(int q, int nx, int ny, int nz, const int* bc, const double* f,
                 for (i = 0; i < q; ++i)
                     g[(int64_t)i * cells + x + (int64_t)nx * (y + (int64_t)ny * z)] =
                         f[or_pull_source(&vs, n, bc, i, x, y, z)];
+    return 0;
+}
+
+/* One cell's collision in the chosen homogenization form (0: shift, 1: drag). */
+int oracle_collide_mode(int q, const double* g, double varpi, double tau, const double* F, int mode,
+                        double* out)
+{
+    or_velset vs;
+    if (or_get_velset(q, &vs) || mode < 0 || mode > 1) return -1;
+    if (mode == 1) or_collide_cell_drag(&vs, g, varpi, tau, F, out);
+    else or_collide_cell(&vs, g, varpi, tau, F, out);
+    return 0;
+}
+
+/* As oracle_run with the homogenization form `mode` (0: shift, 1: drag). */
+int oracle_run_mode(int q, int nx, int ny, int nz, const int* bc, double tau, const double* F,
+                    const double* varpi, double* f, double* tmp, long nsteps, int mode)
+{
+    or_velset vs;
+    int n[3] = {nx, ny, nz};
+    int64_t cells = (int64_t)nx * ny * nz;
+    long s;
+    double *src = f, *dst = tmp;
+    if (or_get_velset(q, &vs) || mode < 0 || mode > 1) return -1;
+    if (!(tau > 0.5)) return -1;
+    for (s = 0; s < nsteps; ++s) {
+        int z;
+#pragma omp parallel for schedule(static)
+        for (z = 0; z < nz; ++z) {
+            int x, y, i;
+            double g[OR_MAXQ], out[OR_MAXQ];
+            for (y = 0; y < ny; ++y)
+                for (x = 0; x < nx; ++x) {
+                    int64_t cell = x + (int64_t)nx * (y + (int64_t)ny * z);
+                    or_gather(&vs, n, bc, src, x, y, z, g);
+                    if (mode == 1) or_collide_cell_drag(&vs, g, varpi[cell], tau, F, out);
+                    else or_collide_cell(&vs, g, varpi[cell], tau, F, out);
+                    for (i = 0; i < q; ++i) dst[(int64_t)i * cells + cell] = out[i];
+                }
+        }
+        {
+            double* t = src;
+            src = dst;
+            dst = t;
+        }
+    }
+    if (src != f) memcpy(f, src, sizeof(double) * (size_t)(cells * q));
+    return 0;
+}
+
+/* nsteps of the anisotropic form; varpi3 is [3][cells] (x, y, z components). */
+int oracle_run_aniso(int q, int nx, int ny, int nz, const int* bc, double tau, const double* F,
+                     const double* varpi3, double* f, double* tmp, long nsteps)
+{
+    or_velset vs;
+    int n[3] = {nx, ny, nz};
+    int64_t cells = (int64_t)nx * ny * nz;
+    long s;
+    double *src = f, *dst = tmp;
+    if (or_get_velset(q, &vs) || !(tau > 0.5)) return -1;
+    for (s = 0; s < nsteps; ++s) {
+        int z;
+#pragma omp parallel for schedule(static)
+        for (z = 0; z < nz; ++z) {
+            int x, y, i;
+            double g[OR_MAXQ], out[OR_MAXQ], vp[3];
+            for (y = 0; y < ny; ++y)
+                for (x = 0; x < nx; ++x) {
+                    int64_t cell = x + (int64_t)nx * (y + (int64_t)ny * z);
+                    vp[0] = varpi3[cell];
+                    vp[1] = varpi3[cells + cell];
+                    vp[2] = varpi3[2 * cells + cell];
+                    or_gather(&vs, n, bc, src, x, y, z, g);
+                    or_collide_cell_aniso(&vs, g, vp, tau, F, out);
+                    for (i = 0; i < q; ++i) dst[(int64_t)i * cells + cell] = out[i];
+                }
+        }
+        {
+            double* t = src;
+            src = dst;
+            dst = t;
+        }
+    }
+    if (src != f) memcpy(f, src, sizeof(double) * (size_t)(cells * q));
+    return 0;
+}
+
+/* Resolved obstacles: solid[cell] != 0 marks a solid cell. A fluid cell whose
+ * pull source is solid takes the bounce-back population of its own opposite
+ * direction (half-way bounce-back on the solid surface, no slip); solid cells
+ * are not updated (their populations are left as they are and never read).
+ * Used with varpi = 1 in the fluid for the resolved pore-scale problem whose
+ * permeability the homogenized field approximates (Thm. thmStatNSECase4,
+ * unit-cell problem for A). */
+int oracle_run_masked(int q, int nx, int ny, int nz, const int* bc, double tau, const double* F,
+                      const double* varpi, const unsigned char* solid, double* f, double* tmp, long nsteps)
+{
+    or_velset vs;
+    int n[3] = {nx, ny, nz};
+    int64_t cells = (int64_t)nx * ny * nz;
+    long s;
+    double *src = f, *dst = tmp;
+    if (or_get_velset(q, &vs) || !(tau > 0.5)) return -1;
+    for (s = 0; s < nsteps; ++s) {
+        int z;
+#pragma omp parallel for schedule(static)
+        for (z = 0; z < nz; ++z) {
+            int x, y, i, d;
+            double g[OR_MAXQ], out[OR_MAXQ];
+            for (y = 0; y < ny; ++y)
+                for (x = 0; x < nx; ++x) {
+                    int64_t cell = x + (int64_t)nx * (y + (int64_t)ny * z);
+                    if (solid[cell]) {
+                        for (i = 0; i < q; ++i) dst[(int64_t)i * cells + cell] = src[(int64_t)i * cells + cell];
+                        continue;
+                    }
+                    for (i = 0; i < q; ++i) {
+                        int p[3] = {x, y, z}, sp[3], wall = 0;
+                        for (d = 0; d < 3; ++d) {
+                            sp[d] = p[d] - vs.c[i][d];
+                            if (sp[d] < 0 || sp[d] >= n[d]) {
+                                if (bc[d]) wall = 1;
+                                else sp[d] = (sp[d] + n[d]) % n[d];
+                            }
+                        }
+                        if (!wall && solid[sp[0] + (int64_t)nx * (sp[1] + (int64_t)ny * sp[2])]) wall = 1;
+                        g[i] = wall ? src[(int64_t)vs.opp[i] * cells + cell]
+                                    : src[(int64_t)i * cells + sp[0] + (int64_t)nx * (sp[1] + (int64_t)ny * sp[2])];
+                    }
+                    or_collide_cell(&vs, g, varpi[cell], tau, F, out);
+                    for (i = 0; i < q; ++i) dst[(int64_t)i * cells + cell] = out[i];
+                }
+        }
+        {
+            double* t = src;
+            src = dst;
+            dst = t;
+        }
+    }
+    if (src != f) memcpy(f, src, sizeof(double) * (size_t)(cells * q));
+    return 0;
+}
+
+/* Moments with resolved obstacles: solid cells report rho = 1, u = 0; fluid
+ * cells the moments of their streamed populations (bounce-back at solid
+ * sources). */
+int oracle_moments_masked(int q, int nx, int ny, int nz, const int* bc, const double* F,
+                          const unsigned char* solid, const double* f, double* rho, double* u)
+{
+    or_velset vs;
+    int n[3] = {nx, ny, nz}, x, y, z, i, d;
+    int64_t cells = (int64_t)nx * ny * nz;
+    if (or_get_velset(q, &vs)) return -1;
+    for (z = 0; z < nz; ++z)
+        for (y = 0; y < ny; ++y)
+            for (x = 0; x < nx; ++x) {
+                double g[OR_MAXQ], r, uu[3];
+                int64_t cell = x + (int64_t)nx * (y + (int64_t)ny * z);
+                if (solid[cell]) {
+                    rho[cell] = 1.0;
+                    u[cell] = u[cells + cell] = u[2 * cells + cell] = 0.0;
+                    continue;
+                }
+                for (i = 0; i < q; ++i) {
+                    int p[3] = {x, y, z}, sp[3], wall = 0;
+                    for (d = 0; d < 3; ++d) {
+                        sp[d] = p[d] - vs.c[i][d];
+                        if (sp[d] < 0 || sp[d] >= n[d]) {
+                            if (bc[d]) wall = 1;
+                            else sp[d] = (sp[d] + n[d]) % n[d];
+                        }
+                    }
+                    if (!wall && solid[sp[0] + (int64_t)nx * (sp[1] + (int64_t)ny * sp[2])]) wall = 1;
+                    g[i] = wall ? f[(int64_t)vs.opp[i] * cells + cell]
+                                : f[(int64_t)i * cells + sp[0] + (int64_t)nx * (sp[1] + (int64_t)ny * sp[2])];
+                }
+                or_moments_cell(&vs, g, F, &r, uu);
+                rho[cell] = r;
+                u[cell] = uu[0];
+                u[cells + cell] = uu[1];
+                u[2 * cells + cell] = uu[2];
+            }
+    return 0;
+}
+
+/* One cell's anisotropic collision (varpi3 = 3 values). */
+int oracle_collide_aniso(int q, const double* g, const double* varpi3, double tau, const double* F, double* out)
+{
+    or_velset vs;
+    if (or_get_velset(q, &vs)) return -1;
+    or_collide_cell_aniso(&vs, g, varpi3, tau, F, out);
+    return 0;
+}
+
+/* Density and velocity of a state as the collision of `mode` sees them. */
+int oracle_moments_mode(int q, int nx, int ny, int nz, const int* bc, double tau, const double* F,
+                        const double* varpi, const double* f, int mode, double* rho, double* u)
+{
+    or_velset vs;
+    int n[3] = {nx, ny, nz}, x, y, z;
+    int64_t cells = (int64_t)nx * ny * nz;
+    if (or_get_velset(q, &vs) || mode < 0 || mode > 1) return -1;
+    for (z = 0; z < nz; ++z)
+        for (y = 0; y < ny; ++y)
+            for (x = 0; x < nx; ++x) {
+                double g[OR_MAXQ], r, uu[3];
+                int64_t cell = x + (int64_t)nx * (y + (int64_t)ny * z);
+                or_gather(&vs, n, bc, f, x, y, z, g);
+                or_velocity_mode(&vs, g, varpi[cell], tau, F, mode, &r, uu);
+                rho[cell] = r;
+                u[cell] = uu[0];
+                u[cells + cell] = uu[1];
+                u[2 * cells + cell] = uu[2];
+            }
     return 0;
 }
 

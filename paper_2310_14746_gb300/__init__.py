@@ -47,6 +47,8 @@ HLBM_TWO_LATTICE = 0
 HLBM_AA = 1
 HLBM_PERIODIC = 0
 HLBM_HALFWAY_BOUNCE_BACK = 1
+HLBM_HOMOG_SHIFT = 0
+HLBM_HOMOG_DRAG = 1
 
 STORAGE_BYTES = {HLBM_F64: 8, HLBM_F32: 4, HLBM_F16DEV: 2, HLBM_BF16DEV: 2}
 STORAGE_NAMES = {HLBM_F64: "f64", HLBM_F32: "f32", HLBM_F16DEV: "f16dev", HLBM_BF16DEV: "bf16dev"}
@@ -114,10 +116,13 @@ SIGNATURES = {
     "hlbm_set_stream": (_i, [_vp, _vp]),
     "hlbm_set_relaxation": (_i, [_vp, _d]),
     "hlbm_set_porosity": (_i, [_vp, _vp, _i]),
+    "hlbm_set_porosity_tensor": (_i, [_vp, _vp, _i]),
+    "hlbm_set_solid_mask": (_i, [_vp, _vp, _i]),
     "hlbm_porosity_from_permeability": (_i, [_vp, _d, _d, _vp, ctypes.c_size_t]),
     "hlbm_set_force": (_i, [_vp, _d, _d, _d]),
     "hlbm_set_boundary": (_i, [_vp, _i, _i]),
     "hlbm_set_storage_scale": (_i, [_vp, _d]),
+    "hlbm_set_homogenization": (_i, [_vp, _i]),
     "hlbm_init_equilibrium": (_i, [_vp, _d, _d, _d, _d]),
     "hlbm_set_populations": (_i, [_vp, _vp, _i]),
     "hlbm_get_populations": (_i, [_vp, _vp, _i]),
@@ -224,6 +229,26 @@ def hlbm_set_porosity(h, varpi):
     _check(_lib().hlbm_set_porosity(h, p, dev), "hlbm_set_porosity")
 
 
+def hlbm_set_porosity_tensor(h, varpi3):
+    p, dev = _ptr(varpi3, np.float32)
+    _check(_lib().hlbm_set_porosity_tensor(h, p, dev), "hlbm_set_porosity_tensor")
+
+
+def hlbm_set_solid_mask(h, solid):
+    """solid: uint8 numpy array (host) or uint8 CUDA tensor, nonzero = solid; None removes the mask."""
+    if solid is None:
+        _check(_lib().hlbm_set_solid_mask(h, None, 0), "hlbm_set_solid_mask")
+        return
+    if isinstance(solid, np.ndarray):
+        a = np.ascontiguousarray(solid, dtype=np.uint8)
+        _check(_lib().hlbm_set_solid_mask(h, a.ctypes.data, 0), "hlbm_set_solid_mask")
+        return
+    import torch
+    if not (isinstance(solid, torch.Tensor) and solid.dtype == torch.uint8 and solid.is_contiguous()):
+        raise TypeError("expected a contiguous uint8 array or CUDA tensor")
+    _check(_lib().hlbm_set_solid_mask(h, solid.data_ptr(), 1 if solid.is_cuda else 0), "hlbm_set_solid_mask")
+
+
 def hlbm_porosity_from_permeability(K, nu, tau):
     K = np.ascontiguousarray(K, dtype=np.float32)
     out = np.empty_like(K)
@@ -238,6 +263,10 @@ def hlbm_set_force(h, Fx, Fy, Fz=0.0):
 
 def hlbm_set_boundary(h, axis, kind):
     _check(_lib().hlbm_set_boundary(h, axis, kind), "hlbm_set_boundary")
+
+
+def hlbm_set_homogenization(h, form):
+    _check(_lib().hlbm_set_homogenization(h, int(form)), "hlbm_set_homogenization")
 
 
 def hlbm_set_storage_scale(h, s):
@@ -436,6 +465,12 @@ class Lattice:
     def set_porosity(self, varpi):
         hlbm_set_porosity(self.h, varpi)
 
+    def set_solid_mask(self, solid):
+        hlbm_set_solid_mask(self.h, solid)
+
+    def set_porosity_tensor(self, varpi3):
+        hlbm_set_porosity_tensor(self.h, varpi3)
+
     def set_force(self, Fx, Fy=0.0, Fz=0.0):
         hlbm_set_force(self.h, Fx, Fy, Fz)
 
@@ -444,6 +479,9 @@ class Lattice:
 
     def set_storage_scale(self, s):
         hlbm_set_storage_scale(self.h, s)
+
+    def set_homogenization(self, form):
+        hlbm_set_homogenization(self.h, form)
 
     def init_equilibrium(self, rho0=1.0, u0=(0.0, 0.0, 0.0)):
         hlbm_init_equilibrium(self.h, rho0, *u0)

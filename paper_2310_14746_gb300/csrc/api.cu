@@ -44,12 +44,16 @@ struct hlbm_lattice {
     double F[3] = {0.0, 0.0, 0.0};
     int bc[3] = {HLBM_PERIODIC, HLBM_PERIODIC, HLBM_PERIODIC};
     double scale = 1.0;
+    int homog = HLBM_HOMOG_SHIFT;
     size_t cells = 0;
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;     // two-lattice: buffer holding the state
     int aa_odd = 0;  // AA: 1 when the state is in the SWAPPED layout
     long long step = 0;
     float* varpi = nullptr;
+    float* varpi3 = nullptr;  // diagonal porosity tensor (allocated on first use)
+    int aniso = 0;
+    unsigned* links = nullptr;  // solid-link masks (resolved obstacles), or null
     void* u_prev = nullptr;
     double* partials = nullptr;
     double* out8 = nullptr;
@@ -76,6 +80,10 @@ struct hlbm_lattice {
         for (int a = 0; a < 3; ++a) c.F[a] = F[a];
         c.scale = scale;
         c.stream = s;
+        c.drag = homog == HLBM_HOMOG_DRAG;
+        c.varpi = varpi;
+        c.varpi3 = aniso ? varpi3 : nullptr;
+        c.links = links;
         return c;
     }
 };
@@ -100,6 +108,8 @@ void free_all(hlbm_t* h) {
     cudaFree(h->buf[0]);
     cudaFree(h->buf[1]);
     cudaFree(h->varpi);
+    cudaFree(h->varpi3);
+    cudaFree(h->links);
     cudaFree(h->u_prev);
     cudaFree(h->partials);
     cudaFree(h->out8);
@@ -304,6 +314,7 @@ int hlbm_set_boundary(hlbm_t* h, int axis, int type) {
     if (type != HLBM_PERIODIC && type != HLBM_HALFWAY_BOUNCE_BACK) return HLBM_ERR_INVALID_ARG;
     if (h->q == HLBM_D2Q9 && axis == 2 && type != HLBM_PERIODIC) return HLBM_ERR_INVALID_ARG;
     if (h->bc[axis] == type) return HLBM_OK;
+    if (h->links) return HLBM_ERR_STATE;  // set boundaries before the solid mask
     if (h->pattern == HLBM_AA) {
         // The AA layouts place bounced populations according to the walls:
         // re-lay the post-collision state under the new boundary.
@@ -317,6 +328,14 @@ int hlbm_set_boundary(hlbm_t* h, int axis, int type) {
         if (e != cudaSuccess) return cuda_fail(e);
     }
     h->bc[axis] = type;
+    h->graph_dirty = true;
+    return HLBM_OK;
+}
+
+int hlbm_set_homogenization(hlbm_t* h, int form) {
+    if (!h || (form != HLBM_HOMOG_SHIFT && form != HLBM_HOMOG_DRAG)) return HLBM_ERR_INVALID_ARG;
+    if (form == HLBM_HOMOG_DRAG && h->aniso) return HLBM_ERR_STATE;  // the tensor form is a shift form
+    h->homog = form;
     h->graph_dirty = true;
     return HLBM_OK;
 }
@@ -354,6 +373,8 @@ int hlbm_set_porosity(hlbm_t* h, const float* varpi, int on_device) {
             if (!(varpi[k] >= 0.0f && varpi[k] <= 1.0f)) return HLBM_ERR_INVALID_ARG;
         HLBM_CUDA(cudaMemcpyAsync(h->varpi, varpi, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
         HLBM_CUDA(cudaStreamSynchronize(h->stream));
+        h->aniso = 0;
+        h->graph_dirty = true;
         return HLBM_OK;
     }
     int* bad = nullptr;
@@ -367,6 +388,68 @@ int hlbm_set_porosity(hlbm_t* h, const float* varpi, int on_device) {
     if (e != cudaSuccess) return cuda_fail(e);
     if (nbad) return HLBM_ERR_INVALID_ARG;
     HLBM_CUDA(cudaMemcpyAsync(h->varpi, varpi, n * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    h->aniso = 0;
+    h->graph_dirty = true;
+    return HLBM_OK;
+}
+
+int hlbm_set_solid_mask(hlbm_t* h, const unsigned char* solid, int on_device) {
+    if (!h) return HLBM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!solid) {  // remove the obstacles
+        if (h->links) {
+            HLBM_CUDA(cudaStreamSynchronize(h->stream));
+            cudaFree(h->links);
+            h->links = nullptr;
+        }
+        h->graph_dirty = true;
+        return HLBM_OK;
+    }
+    // the state's layout (AA) depends on the obstacles: keep the post-collision
+    // state across the change, as hlbm_set_boundary does
+    double* tmp = nullptr;
+    unsigned char* dsolid = nullptr;
+    HLBM_CUDA(cudaMallocAsync(&tmp, (size_t)h->q * h->cells * sizeof(double), h->stream));
+    cudaError_t e = launch_read_state(h->ctx(h->stream), h->layout(), h->state(), tmp);
+    if (e == cudaSuccess && !h->links) e = cudaMalloc(&h->links, h->cells * sizeof(unsigned));
+    if (e == cudaSuccess && !on_device) e = cudaMallocAsync(&dsolid, h->cells, h->stream);
+    if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(dsolid, solid, h->cells, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_build_links(h->ctx(h->stream), on_device ? solid : dsolid, h->links);
+    if (e == cudaSuccess) e = launch_write_state(h->ctx(h->stream), h->layout(), tmp, 0, h->state());
+    if (dsolid) cudaFreeAsync(dsolid, h->stream);
+    cudaFreeAsync(tmp, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->graph_dirty = true;
+    return HLBM_OK;
+}
+
+int hlbm_set_porosity_tensor(hlbm_t* h, const float* varpi3, int on_device) {
+    if (!h || !varpi3) return HLBM_ERR_INVALID_ARG;
+    if (h->homog != HLBM_HOMOG_SHIFT) return HLBM_ERR_STATE;
+    DeviceGuard g(h->device);
+    const size_t n = 3 * h->cells;
+    if (!h->varpi3) HLBM_CUDA(cudaMalloc(&h->varpi3, n * sizeof(float)));
+    if (!on_device) {
+        for (size_t k = 0; k < n; ++k)
+            if (!(varpi3[k] >= 0.0f && varpi3[k] <= 1.0f)) return HLBM_ERR_INVALID_ARG;
+        HLBM_CUDA(cudaMemcpyAsync(h->varpi3, varpi3, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        HLBM_CUDA(cudaStreamSynchronize(h->stream));
+    } else {
+        int* bad = nullptr;
+        HLBM_CUDA(cudaMallocAsync(&bad, sizeof(int), h->stream));
+        int nbad = 0;
+        cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), h->stream);
+        if (e == cudaSuccess) e = launch_check_unit_interval(varpi3, n, bad, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFreeAsync(bad, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (nbad) return HLBM_ERR_INVALID_ARG;
+        HLBM_CUDA(cudaMemcpyAsync(h->varpi3, varpi3, n * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    h->aniso = 1;
+    h->graph_dirty = true;
     return HLBM_OK;
 }
 
@@ -549,6 +632,8 @@ int adopt_natural(hlbm_t* h, const void* src, Scratch& sc) {
 int hlbm_adjoint_flux_grad(hlbm_t* h, long nsteps, int every, int plane_x, double* J, float* grad, int on_device) {
     if (!h || !J || !grad || nsteps < 0 || every < 1 || plane_x < 0 || plane_x >= (h ? h->nx : 0))
         return HLBM_ERR_INVALID_ARG;
+    // the adjoint differentiates the isotropic shift form without obstacles
+    if (h->homog != HLBM_HOMOG_SHIFT || h->aniso || h->links) return HLBM_ERR_STATE;
     DeviceGuard g(h->device);
     const size_t sb = h->state_bytes();
     const size_t N = h->cells;
@@ -629,6 +714,7 @@ int hlbm_save(hlbm_t* h, const char* path) {
         hd.bc[a] = h->bc[a];
     }
     hd.scale = h->scale;
+    hd.pad = h->homog;
     FILE* fp = std::fopen(path, "wb");
     if (!fp) return HLBM_ERR_IO;
     bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1 && std::fwrite(st.data(), 1, st.size(), fp) == st.size() &&
@@ -662,6 +748,7 @@ int hlbm_load(hlbm_t* h, const char* path) {
         h->bc[a] = hd.bc[a];
     }
     h->scale = hd.scale;
+    h->homog = hd.pad == HLBM_HOMOG_DRAG ? HLBM_HOMOG_DRAG : HLBM_HOMOG_SHIFT;
     h->graph_dirty = true;
     HLBM_CUDA(cudaMemcpyAsync(h->buf[0], st.data(), st.size(), cudaMemcpyHostToDevice, h->stream));
     HLBM_CUDA(cudaMemcpyAsync(h->varpi, vp.data(), vp.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));

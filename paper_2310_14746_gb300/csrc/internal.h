@@ -20,7 +20,17 @@ struct LaunchCtx {
     double F[3];
     double scale;   // storage scale s (deviations are stored times s)
     cudaStream_t stream;
+    int drag = 0;                  // homogenization form: 0 equilibrium shift, 1 explicit drag
+    const float* varpi = nullptr;  // porosity control (observables need it in the drag form)
+    const float* varpi3 = nullptr; // diagonal porosity tensor [3][cells], or null (isotropic)
+    const unsigned* links = nullptr; // solid-link masks (resolved obstacles), or null
 };
+
+// Solid-link masks from a solid flag per cell (uint8, nonzero = solid): bit i of
+// links[cell] is set when the pull source x - c_i is solid (periodic wrap; a
+// source beyond a domain wall is left to the wall logic), bit 31 when the
+// cell itself is solid.
+cudaError_t launch_build_links(const LaunchCtx& c, const unsigned char* solid, unsigned* links);
 
 // One time step: read `fin` in the layout implied by `mode`, write `fout`
 // (== fin for the AA modes).

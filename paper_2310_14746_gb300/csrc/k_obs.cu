@@ -26,14 +26,20 @@ static Phys<C> phys(const LaunchCtx& c) {
 template <int Q, class S, bool WALLS, class Out>
 __global__ void __launch_bounds__(256)
 k_moments(const typename S::T* f, int lay, Geometry g, Phys<typename S::C> ph, typename S::C inv_s,
-          Out* rho, Out* u) {
+          Out* rho, Out* u, const float* varpi, int drag, const unsigned* links) {
     using C = typename S::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const Nbr<long long> nb(g, x, y, z);
     const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
+    const unsigned lm = links ? links[cell] : 0u;
+    if (lm & kSolidBit) {  // resolved obstacle: at rest
+        if (rho) rho[cell] = Out(1);
+        if (u) u[cell] = u[g.N + cell] = u[2 * g.N + cell] = Out(0);
+        return;
+    }
+    const Nbr<long long> nb(g, x, y, z, lm);
     C d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = S::load(f, gather_index<Q, WALLS>(g, nb, cell, i, lay), inv_s);
@@ -43,7 +49,7 @@ k_moments(const typename S::T* f, int lay, Geometry g, Phys<typename S::C> ph, t
     if (rho) rho[cell] = Out(r);
     if (u) {
         C ux, uy, uz;
-        velocity<C>(jx, jy, jz, C(1) / r, ph, ux, uy, uz);
+        velocity_form<C>(jx, jy, jz, r, drag ? C(varpi[cell]) : C(1), drag, ph, ux, uy, uz);
         u[cell] = Out(ux);
         u[g.N + cell] = Out(uy);
         u[2 * g.N + cell] = Out(uz);
@@ -59,10 +65,10 @@ static cudaError_t moments_impl(const LaunchCtx& c, int lay, const void* f, void
     const auto* a = static_cast<const typename S::T*>(f);
     if (f64)
         k_moments<Q, S, WALLS, double><<<grd, blk, 0, c.stream>>>(a, lay, g, phys<C, Q>(c), C(1.0 / c.scale),
-                                                                  (double*)rho, (double*)u);
+                                                                  (double*)rho, (double*)u, c.varpi, c.drag, c.links);
     else
         k_moments<Q, S, WALLS, float><<<grd, blk, 0, c.stream>>>(a, lay, g, phys<C, Q>(c), C(1.0 / c.scale),
-                                                                 (float*)rho, (float*)u);
+                                                                 (float*)rho, (float*)u, c.varpi, c.drag, c.links);
     return cudaGetLastError();
 }
 
@@ -86,29 +92,37 @@ __device__ __forceinline__ double warp_max(double v) {
 template <int Q, class S, bool WALLS>
 __global__ void __launch_bounds__(256)
 k_reduce_partials(const typename S::T* f, int lay, Geometry g, Phys<typename S::C> ph,
-                  typename S::C inv_s, typename S::C* u_prev, int update_prev, double* partials) {
+                  typename S::C inv_s, typename S::C* u_prev, int update_prev, double* partials, const float* varpi,
+                  int drag, const unsigned* links) {
     using C = typename S::C;
     __shared__ double sh[8][8];  // [warp][quantity]
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (x < g.nx && y < g.ny) {
-        const Nbr<long long> nb(g, x, y, z);
-        const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
+    const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
+    const unsigned lm = (links && x < g.nx && y < g.ny) ? links[cell] : 0u;
+    if (x < g.nx && y < g.ny && (lm & kSolidBit)) {
+        // resolved obstacle: rho = 1, u = 0 (contributes nothing but its residual reference)
+        if (update_prev)
+            for (int k = 0; k < 3; ++k) u_prev[k * g.N + cell] = typename S::C(0);
+    } else if (x < g.nx && y < g.ny) {
+        const Nbr<long long> nb(g, x, y, z, lm);
         C d[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) d[i] = S::load(f, gather_index<Q, WALLS>(g, nb, cell, i, lay), inv_s);
         C drho, jx, jy, jz;
         moments<Q, C>(d, drho, jx, jy, jz);
         C u3[3];
-        velocity<C>(jx, jy, jz, C(1) / (C(1) + drho), ph, u3[0], u3[1], u3[2]);
-        // rho*u = j + F/2, formed in FP64
-        const double mx = (double)jx + 0.5 * (double)ph.Fx;
+        const C vp = drag ? C(varpi[cell]) : C(1);
+        velocity_form<C>(jx, jy, jz, C(1) + drho, vp, drag, ph, u3[0], u3[1], u3[2]);
+        // rho*u = (j + F/2) (/(1 + lam/2) in the drag form), formed in FP64
+        const double hd = drag ? 1.0 / (1.0 + 0.5 * (1.0 - (double)vp) * (double)ph.omega) : 1.0;
+        const double mx = ((double)jx + 0.5 * (double)ph.Fx) * hd;
         v[0] = (double)drho;
         v[1] = mx;
-        v[2] = (double)jy + 0.5 * (double)ph.Fy;
-        v[3] = (double)jz + 0.5 * (double)ph.Fz;
+        v[2] = ((double)jy + 0.5 * (double)ph.Fy) * hd;
+        v[3] = ((double)jz + 0.5 * (double)ph.Fz) * hd;
         v[4] = (x == g.nx - 1) ? mx : 0.0;
         double du = 0.0, um = 0.0;
 #pragma unroll
@@ -180,7 +194,8 @@ static cudaError_t reduce_impl(const LaunchCtx& c, int lay, const void* f, void*
     const dim3 grd((c.nx + blk.x - 1) / blk.x, (c.ny + blk.y - 1) / blk.y, c.nz);
     k_reduce_partials<Q, S, WALLS><<<grd, blk, 0, c.stream>>>(static_cast<const typename S::T*>(f), lay, g,
                                                               phys<C, Q>(c), C(1.0 / c.scale),
-                                                              static_cast<C*>(u_prev), upd, partials);
+                                                              static_cast<C*>(u_prev), upd, partials, c.varpi,
+                                                              c.drag, c.links);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_final<<<1, 256, 0, c.stream>>>(partials, reduce_partials_count(c), (double)g.N,
@@ -193,15 +208,18 @@ static cudaError_t reduce_impl(const LaunchCtx& c, int lay, const void* f, void*
 // ---------------------------------------------------------------------------
 template <int Q, class S, bool WALLS>
 __global__ void __launch_bounds__(256)
-k_write_state(const double* fnat, int uniform, int lay, Geometry g, typename S::C s, typename S::T* f) {
+k_write_state(const double* fnat, int uniform, int lay, Geometry g, typename S::C s, typename S::T* f,
+              const unsigned* links) {
     using C = typename S::C;
     using L = Lat<Q>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const Nbr<long long> nb(g, x, y, z);
     const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
+    const unsigned lm = links ? links[cell] : 0u;
+    if (lm & kSolidBit) return;  // solid cells hold no state (their slots may belong to neighbours)
+    const Nbr<long long> nb(g, x, y, z, lm);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const double fi = uniform ? fnat[i] : fnat[(size_t)i * g.N + cell];
@@ -211,14 +229,21 @@ k_write_state(const double* fnat, int uniform, int lay, Geometry g, typename S::
 
 template <int Q, class S, bool WALLS>
 __global__ void __launch_bounds__(256)
-k_read_state(const typename S::T* f, int lay, Geometry g, typename S::C inv_s, double* fnat) {
+k_read_state(const typename S::T* f, int lay, Geometry g, typename S::C inv_s, double* fnat,
+             const unsigned* links) {
     using L = Lat<Q>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const Nbr<long long> nb(g, x, y, z);
     const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
+    const unsigned lm = links ? links[cell] : 0u;
+    if (lm & kSolidBit) {  // solid cells read as the rest state
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fnat[(size_t)i * g.N + cell] = L::w(i);
+        return;
+    }
+    const Nbr<long long> nb(g, x, y, z, lm);
 #pragma unroll
     for (int i = 0; i < Q; ++i)
         fnat[(size_t)i * g.N + cell] =
@@ -231,7 +256,7 @@ static cudaError_t write_impl(const LaunchCtx& c, int lay, const double* fnat, i
     const dim3 blk = block_for(c.nx);
     const dim3 grd((c.nx + blk.x - 1) / blk.x, (c.ny + blk.y - 1) / blk.y, c.nz);
     k_write_state<Q, S, WALLS><<<grd, blk, 0, c.stream>>>(fnat, uniform, lay, geom(c), C(c.scale),
-                                                          static_cast<typename S::T*>(f));
+                                                          static_cast<typename S::T*>(f), c.links);
     return cudaGetLastError();
 }
 
@@ -241,7 +266,7 @@ static cudaError_t read_impl(const LaunchCtx& c, int lay, const void* f, double*
     const dim3 blk = block_for(c.nx);
     const dim3 grd((c.nx + blk.x - 1) / blk.x, (c.ny + blk.y - 1) / blk.y, c.nz);
     k_read_state<Q, S, WALLS><<<grd, blk, 0, c.stream>>>(static_cast<const typename S::T*>(f), lay, geom(c),
-                                                         C(1.0 / c.scale), fnat);
+                                                         C(1.0 / c.scale), fnat, c.links);
     return cudaGetLastError();
 }
 
@@ -250,7 +275,7 @@ static cudaError_t read_impl(const LaunchCtx& c, int lay, const void* f, double*
 // ---------------------------------------------------------------------------
 template <int Q, class S, class Fn>
 static cudaError_t with_walls(const LaunchCtx& c, Fn&& fn) {
-    const bool walls = c.wall[0] || c.wall[1] || c.wall[2];
+    const bool walls = c.wall[0] || c.wall[1] || c.wall[2] || c.links;
     return walls ? fn.template operator()<Q, S, true>() : fn.template operator()<Q, S, false>();
 }
 template <int Q, class Fn>

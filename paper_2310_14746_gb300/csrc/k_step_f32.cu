@@ -1,0 +1,10 @@
+// Step kernels for the StoreF32 storage policy.
+#include "k_step.cuh"
+
+namespace hlbm {
+
+cudaError_t step_f32(const LaunchCtx& c, int mode, const void* fin, void* fout, const float* varpi) {
+    return step_for_storage<StoreF32>(c, mode, fin, fout, varpi);
+}
+
+}  // namespace hlbm

@@ -161,12 +161,17 @@ struct Geometry {
 // periodic neighbours at -1 / +1 along each axis (wrap folded in), and
 // whether the cell sits at the low / high end of a wall axis. I is the index
 // type: int when q*cells < 2^31 (cheaper address arithmetic), else long long.
+// Resolved obstacles: links[cell] bit i says that the pull source x - c_i is a
+// solid cell (bounce-back on that link), bit 31 that the cell itself is solid.
+constexpr unsigned kSolidBit = 1u << 31;
+
 template <class I = long long>
 struct Nbr {
     I oxm, oxp, oym, oyp, ozm, ozp;
     bool lo_x, hi_x, lo_y, hi_y, lo_z, hi_z;
+    unsigned lm = 0;  // solid-link mask of the cell (0 without obstacles)
 
-    __device__ __forceinline__ Nbr(const Geometry& g, int x, int y, int z) {
+    __device__ __forceinline__ Nbr(const Geometry& g, int x, int y, int z, unsigned links = 0) : lm(links) {
         const I sy = (I)g.nx, sz = (I)g.nx * (I)g.ny;
         oxm = x == 0 ? (I)(g.nx - 1) : (I)-1;
         oxp = x == g.nx - 1 ? (I)(1 - g.nx) : (I)1;
@@ -197,13 +202,15 @@ struct Nbr {
         return o;
     }
 
-    // Does x + s*c_i lie beyond a wall?
+    // Does x + s*c_i lie beyond a wall or in a solid cell? (x + c_i is the pull
+    // source of the opposite direction.)
     template <int Q>
     __device__ __forceinline__ bool beyond_wall(int i, int s) const {
         using L = Lat<Q>;
         const int dx = s * L::cx(i), dy = s * L::cy(i), dz = s * L::cz(i);
+        const int link = s < 0 ? i : opp<Q>(i);
         return (dx < 0 && lo_x) || (dx > 0 && hi_x) || (dy < 0 && lo_y) || (dy > 0 && hi_y) ||
-               (dz < 0 && lo_z) || (dz > 0 && hi_z);
+               (dz < 0 && lo_z) || (dz > 0 && hi_z) || ((lm >> link) & 1u);
     }
 };
 
@@ -399,6 +406,122 @@ __device__ __forceinline__ void collide(C* d, C varpi, const Phys<C>& ph, C s = 
         d[i] = fma_(keep, d[i], even) + odd;
         d[j] = fma_(keep, d[j], even) - odd;
     }
+}
+
+// Explicit-drag form of the homogenization (Sec. 3.3, eq. momentumHLBM): the
+// equilibrium stays at u and the drag -lam rho u, lam = nu/K = (1 - varpi)/tau,
+// joins the body force, G = F - lam rho u, in Guo's scheme; u is the half-force
+// velocity of the total force, u = (j + F/2) / (rho (1 + lam/2)). With
+// h = 1/(1 + lam/2), rho (c.u) = h (c.j + c.F/2) and c.G = c.F - lam rho (c.u),
+// so the odd part of omega*M_i + S_i is kk (c.j) + (kk/2 + g)(c.F) with
+// kk = (k - g lam) h: the same fma shape as the shift form.
+template <int Q, class C, bool SCALED = false>
+__device__ __forceinline__ void collide_drag(C* d, C varpi, const Phys<C>& ph, C s = C(1), C inv_s = C(1)) {
+    using L = Lat<Q>;
+    C drho_s, jxs, jys, jzs;
+    moments<Q, C>(d, drho_s, jxs, jys, jzs);
+    const C drho = SCALED ? drho_s * inv_s : drho_s;
+    const C jx = SCALED ? jxs * inv_s : jxs, jy = SCALED ? jys * inv_s : jys, jz = SCALED ? jzs * inv_s : jzs;
+    const C rho = C(1) + drho;
+    const C lam = (C(1) - varpi) * ph.omega;
+    const C h = C(1) / fma_(C(0.5), lam, C(1));
+    C ux, uy, uz;
+    velocity<C>(jx, jy, jz, h / rho, ph, ux, uy, uz);
+    const C lr = -lam * rho;
+    const C Gx = fma_(lr, ux, ph.Fx), Gy = fma_(lr, uy, ph.Fy), Gz = fma_(lr, uz, ph.Fz);
+    const C rho_s = SCALED ? rho * s : rho;
+    const C A = fma_(-rho_s, C(1.5) * (ux * ux + uy * uy + uz * uz), drho_s);
+    const C uG3 = C(3) * (ux * Gx + uy * Gy + uz * Gz);
+    const C r45 = C(4.5) * rho_s;
+    const C keep = C(1) - ph.omega;
+    const C guo_s = SCALED ? ph.guo * s : ph.guo;
+    {
+        const C w = C(L::w(0));
+        d[0] = fma_(keep, d[0], fma_(ph.omega * w, A, -(guo_s * w) * uG3));
+    }
+    const C kk1 = fma_(-ph.g1, lam, ph.k1) * h, kk2 = fma_(-ph.g2, lam, ph.k2) * h;
+    const C g1 = SCALED ? ph.g1 * s : ph.g1, g2 = SCALED ? ph.g2 * s : ph.g2;
+    const C kks1 = SCALED ? kk1 * s : kk1, kks2 = SCALED ? kk2 * s : kk2;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int j = opp<Q>(i);
+        if (j < i) continue;
+        const int c2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
+        const C cx = C(L::cx(i)), cy = C(L::cy(i)), cz = C(L::cz(i));
+        const C w = C(L::w(i));
+        const C cu = cx * ux + cy * uy + cz * uz;
+        const C cG = cx * Gx + cy * Gy + cz * Gz;
+        const C cF = cx * ph.Fx + cy * ph.Fy + cz * ph.Fz;
+        const C cj = cx * jxs + cy * jys + cz * jzs;
+        const C kk = c2 == 1 ? kk1 : kk2;
+        const C kks = c2 == 1 ? kks1 : kks2;
+        const C g = c2 == 1 ? g1 : g2;
+        const C even = fma_(ph.omega * w, fma_(r45, cu * cu, A), (guo_s * w) * fma_(C(9) * cu, cG, -uG3));
+        const C odd = fma_(kk, cj, fma_(kks, C(0.5) * cF, g * cF));
+        d[i] = fma_(keep, d[i], even) + odd;
+        d[j] = fma_(keep, d[j], even) - odd;
+    }
+}
+
+// Anisotropic (diagonal-tensor) porosity control: the Maxwellian at
+// v = (vx ux, vy uy, vz uz), a per-axis drag nu/K_a. As collide(), with the
+// odd part k (c.(varpi o j)) + (k/2 c.(varpi o F) + g c.F).
+template <int Q, class C, bool SCALED = false>
+__device__ __forceinline__ void collide_aniso(C* d, C wx, C wy, C wz, const Phys<C>& ph, C s = C(1), C inv_s = C(1)) {
+    using L = Lat<Q>;
+    C drho_s, jxs, jys, jzs;
+    moments<Q, C>(d, drho_s, jxs, jys, jzs);
+    const C drho = SCALED ? drho_s * inv_s : drho_s;
+    const C jx = SCALED ? jxs * inv_s : jxs, jy = SCALED ? jys * inv_s : jys, jz = SCALED ? jzs * inv_s : jzs;
+    const C rho = C(1) + drho;
+    const C inv_rho = C(1) / rho;
+    C ux, uy, uz;
+    velocity<C>(jx, jy, jz, inv_rho, ph, ux, uy, uz);
+    const C vx = wx * ux, vy = wy * uy, vz = wz * uz;
+    const C rho_s = SCALED ? rho * s : rho;
+    const C A = fma_(-rho_s, C(1.5) * (vx * vx + vy * vy + vz * vz), drho_s);
+    const C uF3 = C(3) * (ux * ph.Fx + uy * ph.Fy + uz * ph.Fz);
+    const C r45 = C(4.5) * rho_s;
+    const C keep = C(1) - ph.omega;
+    const C guo_s = SCALED ? ph.guo * s : ph.guo;
+    {
+        const C w = C(L::w(0));
+        d[0] = fma_(keep, d[0], fma_(ph.omega * w, A, -(guo_s * w) * uF3));
+    }
+    const C pjx = wx * jxs, pjy = wy * jys, pjz = wz * jzs;             // varpi o j (units of d)
+    const C hFx = C(0.5) * wx * ph.Fx, hFy = C(0.5) * wy * ph.Fy, hFz = C(0.5) * wz * ph.Fz;
+    const C g1 = SCALED ? ph.g1 * s : ph.g1, g2 = SCALED ? ph.g2 * s : ph.g2;
+    const C ks1 = SCALED ? ph.k1 * s : ph.k1, ks2 = SCALED ? ph.k2 * s : ph.k2;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int j = opp<Q>(i);
+        if (j < i) continue;
+        const int c2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
+        const C cx = C(L::cx(i)), cy = C(L::cy(i)), cz = C(L::cz(i));
+        const C w = C(L::w(i));
+        const C cv = cx * vx + cy * vy + cz * vz;
+        const C cu = cx * ux + cy * uy + cz * uz;
+        const C cF = cx * ph.Fx + cy * ph.Fy + cz * ph.Fz;
+        const C cpj = cx * pjx + cy * pjy + cz * pjz;
+        const C cpF = cx * hFx + cy * hFy + cz * hFz;
+        const C k = c2 == 1 ? ph.k1 : ph.k2;
+        const C ks = c2 == 1 ? ks1 : ks2;
+        const C g = c2 == 1 ? g1 : g2;
+        const C even = fma_(ph.omega * w, fma_(r45, cv * cv, A), (guo_s * w) * fma_(C(9) * cu, cF, -uF3));
+        const C odd = fma_(k, cpj, fma_(ks, cpF, g * cF));
+        d[i] = fma_(keep, d[i], even) + odd;
+        d[j] = fma_(keep, d[j], even) - odd;
+    }
+}
+
+// Velocity seen by the collision of either form: u = (j + F/2)/rho for the
+// shift form, divided by (1 + lam/2) for the drag form.
+template <class C>
+__device__ __forceinline__ void velocity_form(C jx, C jy, C jz, C rho, C varpi, int drag, const Phys<C>& ph, C& ux,
+                                              C& uy, C& uz) {
+    C inv = C(1) / rho;
+    if (drag) inv = inv / fma_(C(0.5), (C(1) - varpi) * ph.omega, C(1));
+    velocity<C>(jx, jy, jz, inv, ph, ux, uy, uz);
 }
 
 }  // namespace hlbm
