@@ -43,7 +43,11 @@ FALLBACK_HBM_GBS = 6800.0
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from the
 # ncu capture summarised under profiles/ (None until captured for the current kernel).
-KERNEL_TRAFFIC_BYTES = {}
+KERNEL_TRAFFIC_BYTES = {
+    # k_step<19, StoreF32, periodic, two-lattice, int, shift-fx>, 256^3: mean of two launches
+    # (1342212864 + 1229032448 and 1342241536 + 1218956288 bytes)
+    ("stream_collide_d3q19_f32_two", 256): 2566221568,
+}
 
 WORKLOADS = {
     "d3q19_256_f32": dict(q=19, n=256, storage="f32", pattern="two", tau=0.6, F=(1e-6, 0.0, 0.0),

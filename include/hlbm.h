@@ -177,6 +177,17 @@ int hlbm_set_boundary(hlbm_t* h, int axis, int type);
  * (HLBM_ERR_STATE otherwise). */
 int hlbm_set_homogenization(hlbm_t* h, int form);
 
+/* Which of the equivalent step kernels runs (no counterpart in the paper: an
+ * implementation choice, exposed for testing and measurement).
+ * HLBM_STEP_AUTO (default) picks the fastest kernel that applies: for FP16
+ * and BF16 storage on periodic two-lattice lattices with an even nx, a
+ * kernel that updates two neighbouring cells per thread with 32-bit words.
+ * HLBM_STEP_PER_CELL forces the one-cell-per-thread kernel. Both give
+ * bit-identical states. */
+#define HLBM_STEP_AUTO 0
+#define HLBM_STEP_PER_CELL 1
+int hlbm_set_step_kernel(hlbm_t* h, int variant);
+
 /* Storage scale s of the FP16 deviation policy (a power of two in
  * [1, 2^20]); other policies accept only 1. Applies to later writes of
  * the state: call before hlbm_init_equilibrium / hlbm_set_populations. */
@@ -305,15 +316,23 @@ typedef struct {
  * check_every (even, 2..10000) steps, on `cuda_stream`. With a reduced-
  * precision storage, refinement is on by default: a slot whose residual
  * reaches the storage's rounding floor (floor_coef * max|u|; 2e-3 for FP16,
- * 1.6e-2 for BF16) or stops improving for 20 checks is converted in place to
- * FP32 storage (when the budget allows) and must then meet its tolerance in
- * FP32. */
+ * 1.6e-2 for BF16), or stops improving for 20 checks within 10 times that
+ * floor, is converted in place to FP32 storage (when the budget allows) and
+ * must then meet its tolerance in FP32. Scheduling: every round the oldest
+ * live request advances check_every steps; the other live requests advance
+ * in a `share` of the rounds (default 0.25; hlbm_server_set_priority). */
 int hlbm_server_create(hlbm_server_t** out, size_t mem_budget, int storage, int check_every,
                        void* cuda_stream);
 /* Turn refinement on or off and set its floor coefficient (>= 0). With it off,
  * a reduced-precision slot converges only if its own rounding noise stays
  * below the tolerance. */
 int hlbm_server_set_refinement(hlbm_server_t* s, int enable, double floor_coef);
+/* Age priority of the batch (no counterpart in the paper: a serving policy).
+ * share in (0, 1] is the fraction of rounds in which a live request other
+ * than the oldest one advances; 1 advances every live request every round
+ * (plain processor sharing). Results do not depend on it, only when they
+ * arrive. */
+int hlbm_server_set_priority(hlbm_server_t* s, double share);
 /* Queue a request (validated and copied); *id receives its identifier.
  * HLBM_ERR_OOM if it could never fit the budget. */
 int hlbm_server_submit(hlbm_server_t* s, const hlbm_request* r, uint64_t* id);

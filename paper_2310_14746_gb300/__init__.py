@@ -49,6 +49,8 @@ HLBM_PERIODIC = 0
 HLBM_HALFWAY_BOUNCE_BACK = 1
 HLBM_HOMOG_SHIFT = 0
 HLBM_HOMOG_DRAG = 1
+HLBM_STEP_AUTO = 0
+HLBM_STEP_PER_CELL = 1
 
 STORAGE_BYTES = {HLBM_F64: 8, HLBM_F32: 4, HLBM_F16DEV: 2, HLBM_BF16DEV: 2}
 STORAGE_NAMES = {HLBM_F64: "f64", HLBM_F32: "f32", HLBM_F16DEV: "f16dev", HLBM_BF16DEV: "bf16dev"}
@@ -123,6 +125,7 @@ SIGNATURES = {
     "hlbm_set_boundary": (_i, [_vp, _i, _i]),
     "hlbm_set_storage_scale": (_i, [_vp, _d]),
     "hlbm_set_homogenization": (_i, [_vp, _i]),
+    "hlbm_set_step_kernel": (_i, [_vp, _i]),
     "hlbm_init_equilibrium": (_i, [_vp, _d, _d, _d, _d]),
     "hlbm_set_populations": (_i, [_vp, _vp, _i]),
     "hlbm_get_populations": (_i, [_vp, _vp, _i]),
@@ -136,6 +139,7 @@ SIGNATURES = {
     "hlbm_load": (_i, [_vp, ctypes.c_char_p]),
     "hlbm_server_create": (_i, [ctypes.POINTER(_vp), ctypes.c_size_t, _i, _i, _vp]),
     "hlbm_server_set_refinement": (_i, [_vp, _i, _d]),
+    "hlbm_server_set_priority": (_i, [_vp, _d]),
     "hlbm_server_submit": (_i, [_vp, ctypes.POINTER(hlbm_request), ctypes.POINTER(ctypes.c_uint64)]),
     "hlbm_server_pump": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "hlbm_server_poll": (_i, [_vp, ctypes.POINTER(hlbm_result), _i, ctypes.POINTER(_i)]),
@@ -269,6 +273,10 @@ def hlbm_set_homogenization(h, form):
     _check(_lib().hlbm_set_homogenization(h, int(form)), "hlbm_set_homogenization")
 
 
+def hlbm_set_step_kernel(h, variant):
+    _check(_lib().hlbm_set_step_kernel(h, int(variant)), "hlbm_set_step_kernel")
+
+
 def hlbm_set_storage_scale(h, s):
     _check(_lib().hlbm_set_storage_scale(h, float(s)), "hlbm_set_storage_scale")
 
@@ -359,6 +367,10 @@ def hlbm_server_create(mem_budget, storage=HLBM_F16DEV, check_every=100, stream=
     _check(_lib().hlbm_server_create(ctypes.byref(h), int(mem_budget), storage, check_every, st),
            "hlbm_server_create")
     return h.value
+
+
+def hlbm_server_set_priority(s, share):
+    _check(_lib().hlbm_server_set_priority(s, float(share)), "hlbm_server_set_priority")
 
 
 def hlbm_server_set_refinement(s, enable, floor_coef):
@@ -482,6 +494,9 @@ class Lattice:
 
     def set_homogenization(self, form):
         hlbm_set_homogenization(self.h, form)
+
+    def set_step_kernel(self, variant):
+        hlbm_set_step_kernel(self.h, variant)
 
     def init_equilibrium(self, rho0=1.0, u0=(0.0, 0.0, 0.0)):
         hlbm_init_equilibrium(self.h, rho0, *u0)

@@ -60,6 +60,7 @@ struct hlbm_lattice {
     double* out8_host = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool graph_dirty = true;
+    int step_variant = HLBM_STEP_AUTO;
 
     size_t state_bytes() const { return (size_t)q * cells * storage_bytes(storage); }
     size_t arith_bytes() const { return storage == HLBM_F64 ? 8 : 4; }
@@ -84,6 +85,7 @@ struct hlbm_lattice {
         c.varpi = varpi;
         c.varpi3 = aniso ? varpi3 : nullptr;
         c.links = links;
+        c.variant = step_variant;
         return c;
     }
 };
@@ -336,6 +338,13 @@ int hlbm_set_homogenization(hlbm_t* h, int form) {
     if (!h || (form != HLBM_HOMOG_SHIFT && form != HLBM_HOMOG_DRAG)) return HLBM_ERR_INVALID_ARG;
     if (form == HLBM_HOMOG_DRAG && h->aniso) return HLBM_ERR_STATE;  // the tensor form is a shift form
     h->homog = form;
+    h->graph_dirty = true;
+    return HLBM_OK;
+}
+
+int hlbm_set_step_kernel(hlbm_t* h, int variant) {
+    if (!h || (variant != HLBM_STEP_AUTO && variant != HLBM_STEP_PER_CELL)) return HLBM_ERR_INVALID_ARG;
+    h->step_variant = variant;
     h->graph_dirty = true;
     return HLBM_OK;
 }

@@ -24,6 +24,7 @@ struct LaunchCtx {
     const float* varpi = nullptr;  // porosity control (observables need it in the drag form)
     const float* varpi3 = nullptr; // diagonal porosity tensor [3][cells], or null (isotropic)
     const unsigned* links = nullptr; // solid-link masks (resolved obstacles), or null
+    int variant = 0;                 // 0: fastest applicable step kernel; 1: per-cell kernel only
 };
 
 // Solid-link masks from a solid flag per cell (uint8, nonzero = solid): bit i of
@@ -42,8 +43,8 @@ cudaError_t launch_step(const LaunchCtx& c, int mode, const void* fin, void* fou
 cudaError_t launch_moments(const LaunchCtx& c, int layout, const void* f, void* rho, void* u,
                            int out_f64);
 
-// Per-block FP64 partials of the diagnostics, then a single-block fixed-order
-// final reduction into out8[8] (device). u_prev (arithmetic type of the
+// Per-block FP64 partials of the diagnostics, then a fixed-order final
+// reduction (one block per quantity) into out8[8] (device). u_prev (arithmetic type of the
 // storage: double for F64, float otherwise; 3*cells) is compared against and,
 // if update_prev, overwritten. `partials` is caller-provided scratch of at
 // least reduce_partials_count(c) * 8 doubles.

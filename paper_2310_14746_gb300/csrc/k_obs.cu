@@ -2,6 +2,7 @@
 // conversion, input validation.
 #include "internal.h"
 #include "lattice.cuh"
+#include "diag.cuh"
 
 namespace hlbm {
 
@@ -73,39 +74,28 @@ static cudaError_t moments_impl(const LaunchCtx& c, int lay, const void* f, void
 }
 
 // ---------------------------------------------------------------------------
-// FP64 diagnostics. Stage 1: each block reduces its cells into 8 doubles
-// (sum drho, sum rho*u (3), plane flux, -, max|du|, max|u|) with a fixed
-// shuffle tree. Stage 2: one block folds the block rows in a fixed order.
-// The result does not depend on scheduling.
+// FP64 diagnostics. Stage 1: each block folds its cells into 8 doubles
+// (sum drho, sum rho*u (3), plane flux, 0, max|du|, max|u|) in a fixed order
+// (diag.cuh). Stage 2: one block per column folds the block rows in a fixed
+// order. The result does not depend on scheduling.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    return v;
-}
-
 template <int Q, class S, bool WALLS>
 __global__ void __launch_bounds__(256)
 k_reduce_partials(const typename S::T* f, int lay, Geometry g, Phys<typename S::C> ph,
                   typename S::C inv_s, typename S::C* u_prev, int update_prev, double* partials, const float* varpi,
                   int drag, const unsigned* links) {
     using C = typename S::C;
-    __shared__ double sh[8][8];  // [warp][quantity]
+    __shared__ DiagShared sh;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    DiagCell<C> a;
     const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
     const unsigned lm = (links && x < g.nx && y < g.ny) ? links[cell] : 0u;
     if (x < g.nx && y < g.ny && (lm & kSolidBit)) {
         // resolved obstacle: rho = 1, u = 0 (contributes nothing but its residual reference)
         if (update_prev)
-            for (int k = 0; k < 3; ++k) u_prev[k * g.N + cell] = typename S::C(0);
+            for (int k = 0; k < 3; ++k) u_prev[k * g.N + cell] = C(0);
     } else if (x < g.nx && y < g.ny) {
         const Nbr<long long> nb(g, x, y, z, lm);
         C d[Q];
@@ -116,67 +106,52 @@ k_reduce_partials(const typename S::T* f, int lay, Geometry g, Phys<typename S::
         C u3[3];
         const C vp = drag ? C(varpi[cell]) : C(1);
         velocity_form<C>(jx, jy, jz, C(1) + drho, vp, drag, ph, u3[0], u3[1], u3[2]);
-        // rho*u = (j + F/2) (/(1 + lam/2) in the drag form), formed in FP64
-        const double hd = drag ? 1.0 / (1.0 + 0.5 * (1.0 - (double)vp) * (double)ph.omega) : 1.0;
-        const double mx = ((double)jx + 0.5 * (double)ph.Fx) * hd;
-        v[0] = (double)drho;
-        v[1] = mx;
-        v[2] = ((double)jy + 0.5 * (double)ph.Fy) * hd;
-        v[3] = ((double)jz + 0.5 * (double)ph.Fz) * hd;
-        v[4] = (x == g.nx - 1) ? mx : 0.0;
-        double du = 0.0, um = 0.0;
+        a.fluid = 1;
+        a.plane = x == g.nx - 1;
+        a.s[0] = (double)drho;
+        if (drag) {
+            // rho*u = (j + F/2) / (1 + lam/2), formed in FP64 per cell
+            const double hd = 1.0 / (1.0 + 0.5 * (1.0 - (double)vp) * (double)ph.omega);
+            a.shifted = true;
+            a.s[1] = ((double)jx + 0.5 * (double)ph.Fx) * hd;
+            a.s[2] = ((double)jy + 0.5 * (double)ph.Fy) * hd;
+            a.s[3] = ((double)jz + 0.5 * (double)ph.Fz) * hd;
+        } else {
+            // rho*u = j + F/2: the F/2 is added per block from the fluid-cell count
+            a.s[1] = (double)jx;
+            a.s[2] = (double)jy;
+            a.s[3] = (double)jz;
+        }
+        if (a.plane) a.s[4] = a.s[1];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const C up = u_prev[k * g.N + cell];
-            du = fmax(du, fabs((double)u3[k] - (double)up));
-            um = fmax(um, fabs((double)u3[k]));
+            a.du = nan_max(a.du, C(fabs(u3[k] - up)));
+            a.um = nan_max(a.um, C(fabs(u3[k])));
             if (update_prev) u_prev[k * g.N + cell] = u3[k];
         }
-        v[6] = du;
-        v[7] = um;
     }
-    const int t = threadIdx.x + blockDim.x * threadIdx.y;
-    const int lane = t & 31, warp = t >> 5;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = (k >= 6) ? warp_max(v[k]) : warp_sum(v[k]);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) sh[warp][k] = v[k];
-    __syncthreads();
-    if (t < 8) {
-        double a = sh[0][t];
-        for (int w = 1; w < (int)(blockDim.x * blockDim.y) / 32; ++w) a = (t >= 6) ? fmax(a, sh[w][t]) : a + sh[w][t];
-        const size_t b = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
-        partials[b * 8 + t] = a;
-    }
+    const size_t b = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+    diag_fold<C>(a, sh, threadIdx.x + blockDim.x * threadIdx.y, blockDim.x * blockDim.y, (double)ph.Fx,
+                 (double)ph.Fy, (double)ph.Fz, partials + b * 8);
 }
 
+// Block k folds column k of the partials; block 1 also forms k_app.
 __global__ void __launch_bounds__(256)
 k_reduce_final(const double* partials, size_t nblocks, double cells, double nu, double Fx, double* out8) {
-    __shared__ double sh[8][256];
-    const int t = threadIdx.x;
-    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (size_t b = t; b < nblocks; b += blockDim.x)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = (k >= 6) ? fmax(v[k], partials[b * 8 + k]) : v[k] + partials[b * 8 + k];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) sh[k][t] = v[k];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (t < s)
-#pragma unroll
-            for (int k = 0; k < 8; ++k) sh[k][t] = (k >= 6) ? fmax(sh[k][t], sh[k][t + s]) : sh[k][t] + sh[k][t + s];
-        __syncthreads();
+    __shared__ double buf[256];
+    const int k = blockIdx.x;
+    if (k == 5) {
+        return;  // column 5 is k_app, written by block 1
     }
-    if (t == 0) {
-        out8[0] = cells + sh[0][0];  // mass = sum (1 + drho)
-        out8[1] = sh[1][0];
-        out8[2] = sh[2][0];
-        out8[3] = sh[3][0];
-        out8[4] = sh[4][0];
-        out8[5] = (Fx != 0.0) ? nu * (sh[1][0] / cells) / Fx : 0.0;
-        out8[6] = sh[6][0];
-        out8[7] = sh[7][0];
+    const double v = fold_column(partials, nblocks, k, buf);
+    if (threadIdx.x == 0) {
+        if (k == 0) {
+            out8[0] = cells + v;  // mass = sum (1 + drho)
+        } else {
+            out8[k] = v;
+            if (k == 1) out8[5] = (Fx != 0.0) ? nu * (v / cells) / Fx : 0.0;
+        }
     }
 }
 
@@ -198,7 +173,7 @@ static cudaError_t reduce_impl(const LaunchCtx& c, int lay, const void* f, void*
                                                               c.drag, c.links);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_reduce_final<<<1, 256, 0, c.stream>>>(partials, reduce_partials_count(c), (double)g.N,
+    k_reduce_final<<<8, 256, 0, c.stream>>>(partials, reduce_partials_count(c), (double)g.N,
                                             (c.tau - 0.5) / 3.0, c.F[0], out8);
     return cudaGetLastError();
 }

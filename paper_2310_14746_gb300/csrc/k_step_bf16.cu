@@ -1,10 +1,10 @@
 // Step kernels for the StoreBF16 storage policy.
-#include "k_step.cuh"
+#include "k_step_pair.cuh"
 
 namespace hlbm {
 
 cudaError_t step_bf16(const LaunchCtx& c, int mode, const void* fin, void* fout, const float* varpi) {
-    return step_for_storage<StoreBF16>(c, mode, fin, fout, varpi);
+    return step_for_storage16<StoreBF16>(c, mode, fin, fout, varpi);
 }
 
 }  // namespace hlbm

@@ -1,0 +1,221 @@
+// Two-cells-per-thread stream-and-collide for 16-bit storage (FP16 and BF16
+// deviations), periodic two-lattice lattices with an even nx.
+//
+// The per-cell kernel spends most of its issue slots on work that does not
+// scale with the bytes it moves: 16-bit loads and stores, one conversion per
+// population and per-cell address arithmetic. Here a thread owns the cell
+// pair (x0, x0 + 1), x0 even, and shares the y/z neighbour arithmetic between
+// them:
+//  * c_x = 0: the pair's two populations are one aligned 32-bit word of the
+//    pull source row;
+//  * c_x = +-1: either two aligned words (the pair's word and its left or
+//    right neighbour, merged with one byte permute; LD_WORDS) or two 16-bit
+//    loads (LD_HALVES); L1 serves the overlap between neighbouring threads;
+//  * stores: one 32-bit word per direction, packed by a single paired
+//    conversion.
+// The collision is the same FP32 function as the per-cell kernel, so both
+// kernels produce bit-identical states. A first version that passed the
+// x-shifted halves between lanes with shuffles (so that every load was one
+// aligned word) ran slower than the per-cell kernel: the extra loads of the
+// first and last lane of each row segment and the shuffle latency cost more
+// than the L1 traffic they saved. Register caps matter more than the load
+// scheme: at 64 registers (4 blocks of 256 per SM) the force-along-x form
+// reaches ~0.86 of the measured copy bandwidth, at 96 registers ~0.67.
+#pragma once
+
+#include "k_step.cuh"
+
+namespace hlbm {
+
+template <class S>
+struct Pair16;
+template <>
+struct Pair16<StoreF16> {
+    __device__ static float2 unpack(unsigned w) {
+        __half2 h;
+        memcpy(&h, &w, 4);
+        return __half22float2(h);
+    }
+    __device__ static unsigned pack(float lo, float hi) {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        unsigned w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
+};
+template <>
+struct Pair16<StoreBF16> {
+    __device__ static float2 unpack(unsigned w) {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+    __device__ static unsigned pack(float lo, float hi) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        unsigned w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
+};
+
+// Block width in threads (cell pairs) along x: 64 when it divides the row's
+// pair count, else 32, else the width (up to 128) that leaves the fewest idle
+// threads; short rows take the next power of two.
+inline int pair_block_x(int nx) {
+    const int pairs = nx / 2;
+    if (pairs <= 32) {
+        int b = 1;
+        while (b < pairs) b <<= 1;
+        return b;
+    }
+    if (pairs % 64 == 0) return 64;
+    if (pairs % 32 == 0) return 32;
+    int best = 64, waste_best = 1 << 30;
+    for (int b : {64, 32, 128, 96}) {
+        const int waste = ((pairs + b - 1) / b) * b - pairs;
+        if (waste < waste_best) {
+            best = b;
+            waste_best = waste;
+        }
+    }
+    return best;
+}
+
+enum PairLoad { LD_WORDS = 0, LD_HALVES = 1 };
+
+// The 2 x Q populations the pair (x0, x0 + 1) consumes, as float pairs
+// (d0: cell x0, d1: cell x0 + 1). row_i = plane i at the pull source row of
+// the pair's word (x0, y - c_y, z - c_z); xm1 / xp2 = offsets of x0 - 1 and
+// x0 + 2 within that row (periodic).
+template <int Q, class S, int LD>
+__device__ __forceinline__ void pair_gather(const Planes<const typename S::T, Q>& fin, int cell, const Nbr<int>& nb,
+                                            int xm1, int xp2, float* d0, float* d1) {
+    using L = Lat<Q>;
+    using P = Pair16<S>;
+    using T = typename S::T;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        int o = 0;  // y/z part of the pull offset
+        if (L::cy(i) > 0) o += nb.oym;
+        if (L::cy(i) < 0) o += nb.oyp;
+        if (L::cz(i) > 0) o += nb.ozm;
+        if (L::cz(i) < 0) o += nb.ozp;
+        const T* row = fin.p[i] + (cell + o);
+        if (L::cx(i) == 0) {
+            const float2 f2 = P::unpack(__ldg(reinterpret_cast<const unsigned*>(row)));
+            d0[i] = f2.x;
+            d1[i] = f2.y;
+        } else if (LD == LD_WORDS) {
+            // the word holding x0 - 1 starts at x0 - 2 (xm1 - 1); the one holding x0 + 2 at xp2
+            const unsigned b = __ldg(reinterpret_cast<const unsigned*>(row));
+            const unsigned w = L::cx(i) > 0
+                                   ? __byte_perm(__ldg(reinterpret_cast<const unsigned*>(row + (xm1 - 1))), b, 0x5432)
+                                   : __byte_perm(b, __ldg(reinterpret_cast<const unsigned*>(row + xp2)), 0x5432);
+            const float2 f2 = P::unpack(w);
+            d0[i] = f2.x;
+            d1[i] = f2.y;
+        } else if (L::cx(i) > 0) {  // sources x0 - 1, x0
+            d0[i] = S::load_raw(row + xm1, 0);
+            d1[i] = S::load_raw(row, 0);
+        } else {  // sources x0 + 1, x0 + 2
+            d0[i] = S::load_raw(row + 1, 0);
+            d1[i] = S::load_raw(row + xp2, 0);
+        }
+    }
+}
+
+template <int FORM>
+struct PairTraits {
+    // the force-along-x form fits 64 registers (4 blocks per SM) with word loads; the
+    // others take 80 (3 blocks) with 16-bit loads on the x-shifted directions
+    static constexpr int kMinBlocks = FORM == FORM_SHIFT_FX ? 4 : 3;
+    static constexpr int kLoad = FORM == FORM_SHIFT_FX ? LD_WORDS : LD_HALVES;
+};
+
+template <int Q, class S, int FORM>
+__global__ void __launch_bounds__(256, PairTraits<FORM>::kMinBlocks)
+k_step_pair(Planes<const typename S::T, Q> fin, Planes<typename S::T, Q> fout, const float* __restrict__ varpi,
+            Geometry g, Phys<float> ph, float s, float inv_s, const float* __restrict__ varpi3) {
+    using P = Pair16<S>;
+    const int xp = blockIdx.x * blockDim.x + threadIdx.x;  // pair index along x
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (2 * xp >= g.nx || y >= g.ny) return;
+    const int x0 = 2 * xp;
+    const int cell = x0 + g.nx * (y + g.ny * z);
+    const Nbr<int> nb(g, x0, y, z);
+    const int xm1 = x0 == 0 ? g.nx - 1 : -1;
+    const int xp2 = x0 + 2 >= g.nx ? -x0 : 2;
+
+    float d0[Q], d1[Q];
+    pair_gather<Q, S, PairTraits<FORM>::kLoad>(fin, cell, nb, xm1, xp2, d0, d1);
+
+    if (FORM == FORM_ANISO) {
+        float2 v3[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v3[a] = __ldg(reinterpret_cast<const float2*>(varpi3 + (size_t)a * g.N + cell));
+        collide_aniso<Q, float, S::scaled>(d0, v3[0].x, v3[1].x, v3[2].x, ph, s, inv_s);
+        collide_aniso<Q, float, S::scaled>(d1, v3[0].y, v3[1].y, v3[2].y, ph, s, inv_s);
+    } else {
+        const float2 vp = __ldg(reinterpret_cast<const float2*>(varpi + cell));
+        if (FORM == FORM_DRAG) {
+            collide_drag<Q, float, S::scaled>(d0, vp.x, ph, s, inv_s);
+            collide_drag<Q, float, S::scaled>(d1, vp.y, ph, s, inv_s);
+        } else {
+            collide<Q, float, S::scaled, FORM == FORM_SHIFT_FX>(d0, vp.x, ph, s, inv_s);
+            collide<Q, float, S::scaled, FORM == FORM_SHIFT_FX>(d1, vp.y, ph, s, inv_s);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) *reinterpret_cast<unsigned*>(fout.p[i] + cell) = P::pack(d0[i], d1[i]);
+}
+
+// Launch of the paired kernel; the caller has checked pair_applies().
+template <int Q, class S, int FORM>
+cudaError_t step_pair_impl(const LaunchCtx& c, const void* fin, void* fout, const float* varpi) {
+    using T = typename S::T;
+    Geometry g{c.nx, c.ny, c.nz, 0, 0, 0, (size_t)c.nx * c.ny * c.nz};
+    const Phys<float> ph = make_phys<float, Q>(c.tau, c.F);
+    const int bx = pair_block_x(c.nx);
+    const int by = bx >= 256 ? 1 : 256 / bx;
+    const dim3 blk(bx, by, 1);
+    const dim3 grd((c.nx / 2 + bx - 1) / bx, (c.ny + by - 1) / by, c.nz);
+    Planes<const T, Q> a;
+    Planes<T, Q> b;
+    for (int i = 0; i < Q; ++i) {
+        a.p[i] = static_cast<const T*>(fin) + (size_t)i * g.N;
+        b.p[i] = static_cast<T*>(fout) + (size_t)i * g.N;
+    }
+    k_step_pair<Q, S, FORM><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, float(c.scale), float(1.0 / c.scale),
+                                                       c.varpi3);
+    return cudaGetLastError();
+}
+
+// The paired kernel covers periodic two-lattice steps of lattices with an
+// even nx (aligned pair words in every plane) and 32-bit indices.
+inline bool pair_applies(const LaunchCtx& c, int mode) {
+    return c.variant == 0 && mode == MODE_TWO_LATTICE && !c.wall[0] && !c.wall[1] && !c.wall[2] && !c.links &&
+           c.nx >= 2 && (c.nx % 2) == 0 && (size_t)c.q * c.nx * c.ny * c.nz < ((size_t)1 << 31);
+}
+
+template <int Q, class S>
+cudaError_t step_pair_forms(const LaunchCtx& c, const void* fin, void* fout, const float* varpi) {
+    switch (step_form(c, Q)) {
+        case FORM_SHIFT_FX: return step_pair_impl<Q, S, FORM_SHIFT_FX>(c, fin, fout, varpi);
+        case FORM_SHIFT: return step_pair_impl<Q, S, FORM_SHIFT>(c, fin, fout, varpi);
+        case FORM_DRAG: return step_pair_impl<Q, S, FORM_DRAG>(c, fin, fout, varpi);
+        default: return step_pair_impl<Q, S, FORM_ANISO>(c, fin, fout, varpi);
+    }
+}
+
+// Step kernels of a 16-bit storage policy: the paired kernel where it
+// applies, else the per-cell kernels.
+template <class S>
+cudaError_t step_for_storage16(const LaunchCtx& c, int mode, const void* fin, void* fout, const float* varpi) {
+    if (pair_applies(c, mode)) {
+        if (c.q == 9) return step_pair_forms<9, S>(c, fin, fout, varpi);
+        if (c.q == 19) return step_pair_forms<19, S>(c, fin, fout, varpi);
+        return cudaErrorInvalidValue;
+    }
+    return step_for_storage<S>(c, mode, fin, fout, varpi);
+}
+
+}  // namespace hlbm

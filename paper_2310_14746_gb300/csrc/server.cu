@@ -38,19 +38,22 @@
 #include "../../include/hlbm.h"
 #include "internal.h"
 #include "lattice.cuh"
+#include "diag.cuh"
+#include "k_step_pair.cuh"
 
 namespace hlbm {
 namespace srv {
 
 constexpr int kMaxSlots = 1024;
-constexpr int kBlock = 256;  // threads per block; a tile is tw x (256 / tw) cells of one slot
+constexpr int kBlock = 256;  // threads per block; a tile is tw x (256 / tw) threads of one slot
 
 struct DevSlot {
     void* f[2];
     float* varpi;
     float* u_prev;
     int nx, ny, nz;
-    int tw_log2;  // tile width in x is 2^tw_log2 = min(128, nx rounded up to a power of two >= 32)
+    int pair;     // 16-bit storage with an even nx: a thread owns the cells (2 xp, 2 xp + 1)
+    int tw_log2;  // tile width in threads along x (cells, or cell pairs when `pair`)
     int tiles_x, tiles_y;
     float rcp_tiles_x, rcp_tiles_y;  // 1/tiles_x, 1/tiles_y for the quotient estimate
     int tile_begin;
@@ -65,7 +68,8 @@ struct DevSlot {
 struct DevTable {
     int nslots;
     int total_tiles;
-    int lo[4], hi[4];  // tile range of the slots in each storage (indexed by HLBM_F64..HLBM_BF16DEV)
+    int lo[8], hi[8];       // tile range of each kernel class (kernel_class below)
+    int begin[kMaxSlots];   // first tile of each slot (ascending): the slot lookup reads only this
     DevSlot slot[kMaxSlots];
 };
 
@@ -73,15 +77,47 @@ __device__ __forceinline__ int find_slot(const DevTable* tab, int t, int ns) {
     int lo = 0, hi = ns - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (tab->slot[mid].tile_begin <= t) lo = mid;
+        if (__ldg(&tab->begin[mid]) <= t) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
+// Kernel class of a slot: 2 * storage + 1 for the fast form of its storage (the
+// force along x, and for 16-bit storage the paired cells: the common serving
+// case, compiled on its own for 64 registers), else 2 * storage. The table
+// keeps the slots of a class contiguous.
+__host__ __device__ inline int kernel_class(const DevSlot& d) {
+    const bool fast = d.fx_only && (d.storage == HLBM_F32 || d.pair);
+    return 2 * d.storage + (fast ? 1 : 0);
+}
+
+// Tile geometry of a slot: the tile width is the largest power of two (up to
+// 128) that divides the row's thread count, so the serving edges 32..192
+// leave no idle lanes; rows whose count has no such divisor of at least 16
+// use the next power of two instead.
+inline void set_tiles(DevSlot& d) {
+    d.pair = d.storage != HLBM_F32 && d.nx % 2 == 0;
+    const int w = d.pair ? d.nx / 2 : d.nx;
+    int tw = 1;
+    while (tw < 128 && w % (2 * tw) == 0) tw *= 2;
+    if (tw < 16 && tw < w) {
+        tw = 16;
+        while (tw < 128 && tw < w) tw *= 2;
+    }
+    d.tw_log2 = 0;
+    while ((1 << d.tw_log2) < tw) ++d.tw_log2;
+    const int th = kBlock / tw;
+    d.tiles_x = (w + tw - 1) / tw;
+    d.tiles_y = (d.ny + th - 1) / th;
+    d.rcp_tiles_x = 1.0f / (float)d.tiles_x;
+    d.rcp_tiles_y = 1.0f / (float)d.tiles_y;
+    d.ntiles = d.tiles_x * d.tiles_y * d.nz;
+}
+
 // One cell update of a slot in storage S; launch k of an interval reads f[k&1]
 // and writes f[(k+1)&1] (each interval has an even number of steps).
-template <class S>
+template <class S, bool FX>
 __device__ __forceinline__ void advance_cell(const DevSlot& sl, int k, int x, int y, int z) {
     using C = typename S::C;
     using T = typename S::T;
@@ -95,10 +131,45 @@ __device__ __forceinline__ void advance_cell(const DevSlot& sl, int k, int x, in
 #pragma unroll
     for (int i = 0; i < 19; ++i) d[i] = S::load_raw(fin, gather_index<19, false>(g, nb, cell, i, NATURAL));
     const C vp = C(__ldg(sl.varpi + cell));
-    if (sl.fx_only) collide<19, C, S::scaled, true>(d, vp, ph, C(sl.scale), C(sl.inv_scale));
+    if (FX) collide<19, C, S::scaled, true>(d, vp, ph, C(sl.scale), C(sl.inv_scale));  // the slot's fx_only
     else collide<19, C, S::scaled, false>(d, vp, ph, C(sl.scale), C(sl.inv_scale));
 #pragma unroll
     for (int i = 0; i < 19; ++i) S::store_raw(fout, i * (int)g.N + cell, d[i]);
+}
+
+// Update of the cell pair (x0, x0 + 1) of a 16-bit slot (the paired scheme of
+// the single-lattice 16-bit kernel: shared y/z neighbour arithmetic, 32-bit
+// word loads where the pair's populations share a word, one paired
+// conversion per stored word).
+template <class S, bool FX>
+__device__ __forceinline__ void advance_pair(const DevSlot& sl, int k, int x0, int y, int z) {
+    using P = Pair16<S>;
+    using T = typename S::T;
+    const Geometry g{sl.nx, sl.ny, sl.nz, 0, 0, 0, (size_t)sl.nx * sl.ny * sl.nz};
+    const int N = (int)g.N;
+    Planes<const T, 19> fin;
+    const T* base = static_cast<const T*>(sl.f[k & 1]);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) fin.p[i] = base + i * N;
+    T* fout = static_cast<T*>(sl.f[(k + 1) & 1]);
+    const int cell = x0 + g.nx * (y + g.ny * z);
+    const Nbr<int> nb(g, x0, y, z);
+    const int xm1 = x0 == 0 ? g.nx - 1 : -1;
+    const int xp2 = x0 + 2 >= g.nx ? -x0 : 2;
+    float d0[19], d1[19];
+    const float2 vp = __ldg(reinterpret_cast<const float2*>(sl.varpi + cell));
+    const Phys<float> ph = sl.ph;
+    if (FX) {  // force along x (the slot's fx_only)
+        pair_gather<19, S, LD_WORDS>(fin, cell, nb, xm1, xp2, d0, d1);
+        collide<19, float, S::scaled, true>(d0, vp.x, ph, sl.scale, sl.inv_scale);
+        collide<19, float, S::scaled, true>(d1, vp.y, ph, sl.scale, sl.inv_scale);
+    } else {
+        pair_gather<19, S, LD_HALVES>(fin, cell, nb, xm1, xp2, d0, d1);
+        collide<19, float, S::scaled, false>(d0, vp.x, ph, sl.scale, sl.inv_scale);
+        collide<19, float, S::scaled, false>(d1, vp.y, ph, sl.scale, sl.inv_scale);
+    }
+#pragma unroll
+    for (int i = 0; i < 19; ++i) *reinterpret_cast<unsigned*>(fout + (i * N + cell)) = P::pack(d0[i], d1[i]);
 }
 
 // q = n / d and r = n % d for 0 <= n < 2^21, d >= 1 (a slot has fewer tiles): a float-reciprocal
@@ -117,50 +188,58 @@ __device__ __forceinline__ int divmod(int n, int d, float rcp, int& r) {
     return q;
 }
 
-// Cell of thread `tid` in tile `lt` of a slot (x, y, z); false past the lattice edge.
-__device__ __forceinline__ bool tile_cell(const DevSlot& sl, int lt, int tid, int& x, int& y, int& z) {
+// Thread `tid` of tile `lt` of a slot: its x thread index (a cell, or a cell
+// pair), y and z; false past the lattice edge.
+__device__ __forceinline__ bool tile_cell(const DevSlot& sl, int lt, int tid, int& xt, int& y, int& z) {
     int tx, ty;
     const int rest = divmod(lt, sl.tiles_x, sl.rcp_tiles_x, tx);
     z = divmod(rest, sl.tiles_y, sl.rcp_tiles_y, ty);
     const int tw = 1 << sl.tw_log2;
-    x = tx * tw + (tid & (tw - 1));
+    xt = tx * tw + (tid & (tw - 1));
     y = ty * (kBlock >> sl.tw_log2) + (tid >> sl.tw_log2);
-    return x < sl.nx && y < sl.ny;
+    return xt < (sl.pair ? sl.nx >> 1 : sl.nx) && y < sl.ny;
 }
 
 // One time step of one tile of a live slot stored as S: block b handles tile
-// lo[S] + b of the table (the slots of each storage form one contiguous tile
-// range, so each storage has its own kernel and registers); blocks past the
-// range exit at once. The tile's slot descriptor is staged in shared memory,
-// so its fields are read where they are used instead of held in registers.
-template <class S>
-__global__ void __launch_bounds__(kBlock, 4) k_batched_step(const DevTable* __restrict__ tab, int k) {
+// lo[c] + b of the table, c = 2 * S::kind + FAST (the slots of each kernel
+// class form one contiguous tile range, so each class has its own kernel and
+// register budget); blocks past the range exit at once. The tile's slot
+// descriptor is staged in shared memory, so its fields are read where they
+// are used instead of held in registers.
+template <class S, bool FAST>
+__global__ void __launch_bounds__(kBlock, FAST ? 4 : 3)
+k_batched_step(const DevTable* __restrict__ tab, int k) {
     __shared__ DevSlot sl;
     constexpr int kWords = (int)(sizeof(DevSlot) / sizeof(int));
-    const int t = tab->lo[S::kind] + blockIdx.x;
-    if (t >= tab->hi[S::kind]) return;  // uniform over the block
+    constexpr int cls = 2 * S::kind + (FAST ? 1 : 0);
+    constexpr bool k16 = S::kind == HLBM_F16DEV || S::kind == HLBM_BF16DEV;
+    const int t = tab->lo[cls] + blockIdx.x;
+    if (t >= tab->hi[cls]) return;  // uniform over the block
     if ((int)threadIdx.x < kWords)
         reinterpret_cast<int*>(&sl)[threadIdx.x] =
             reinterpret_cast<const int*>(&tab->slot[find_slot(tab, t, tab->nslots)])[threadIdx.x];
     __syncthreads();
     int x, y, z;
-    if (tile_cell(sl, t - sl.tile_begin, threadIdx.x, x, y, z)) advance_cell<S>(sl, k, x, y, z);
+    if (!tile_cell(sl, t - sl.tile_begin, threadIdx.x, x, y, z)) return;
+    if constexpr (FAST) {  // force along x; 16-bit slots of this class are paired
+        if constexpr (k16) advance_pair<S, true>(sl, k, 2 * x, y, z);
+        else advance_cell<S, true>(sl, k, x, y, z);
+    } else {
+        if constexpr (k16) {
+            if (sl.pair) {  // uniform over the block
+                advance_pair<S, false>(sl, k, 2 * x, y, z);
+                return;
+            }
+        }
+        if (sl.fx_only) advance_cell<S, true>(sl, k, x, y, z);
+        else advance_cell<S, false>(sl, k, x, y, z);
+    }
 }
 
-__device__ __forceinline__ double wsum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ double wmax(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// Diagnostics of one cell of a slot in storage S into v[8] (see k_batched_partials).
+// Diagnostics of one cell of a slot in storage S, added to the thread's
+// accumulator (see k_batched_partials).
 template <class S>
-__device__ __forceinline__ void cell_stats(const DevSlot& sl, int x, int y, int z, double* v) {
+__device__ __forceinline__ void cell_stats(const DevSlot& sl, int x, int y, int z, DiagCell<typename S::C>& a) {
     using C = typename S::C;
     using T = typename S::T;
     const Geometry g{sl.nx, sl.ny, sl.nz, 0, 0, 0, (size_t)sl.nx * sl.ny * sl.nz};
@@ -175,86 +254,71 @@ __device__ __forceinline__ void cell_stats(const DevSlot& sl, int x, int y, int 
     moments<19, C>(d, drho, jx, jy, jz);
     C u3[3];
     velocity<C>(jx, jy, jz, C(1) / (C(1) + drho), ph, u3[0], u3[1], u3[2]);
-    const double mx = (double)jx + 0.5 * (double)ph.Fx;
-    v[0] = drho;
-    v[1] = mx;
-    v[2] = (double)jy + 0.5 * (double)ph.Fy;
-    v[3] = (double)jz + 0.5 * (double)ph.Fz;
-    v[4] = (x == g.nx - 1) ? mx : 0.0;
-    double du = 0.0, um = 0.0;
+    a.fluid += 1;
+    a.s[0] += (double)drho;  // rho*u = j + F/2: F/2 is added per block from the counts
+    a.s[1] += (double)jx;
+    a.s[2] += (double)jy;
+    a.s[3] += (double)jz;
+    if (x == g.nx - 1) {
+        a.plane += 1;
+        a.s[4] += (double)jx;
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        du = fmax(du, fabs((double)u3[c] - (double)sl.u_prev[c * g.N + cell]));
-        um = fmax(um, fabs((double)u3[c]));
+        a.du = nan_max(a.du, fabsf(u3[c] - sl.u_prev[c * g.N + cell]));
+        a.um = nan_max(a.um, fabsf(u3[c]));
         sl.u_prev[c * g.N + cell] = u3[c];
     }
-    v[6] = du;
-    v[7] = um;
 }
 
-// Per-tile FP64 partials of the diagnostics (one block per tile of any slot):
-// sum drho, sum rho*u (3), plane flux, -, max|du|, max|u|.
+// Per-tile FP64 partials of the diagnostics (one block per tile of any slot,
+// the tiles of the step kernel: one or two cells per thread): sum drho, sum
+// rho*u (3), plane flux, 0, max|du|, max|u|; fixed-order fold.
 __global__ void __launch_bounds__(kBlock)
 k_batched_partials(const DevTable* __restrict__ tab, double* __restrict__ partials) {
-    __shared__ double sh[8][8];
+    __shared__ DiagShared sh;
     const int t = blockIdx.x;
     const DevSlot& sl = tab->slot[find_slot(tab, t, tab->nslots)];
-    int x, y, z;
-    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (tile_cell(sl, t - sl.tile_begin, threadIdx.x, x, y, z)) {
-        switch (sl.storage) {
-            case HLBM_F16DEV: cell_stats<StoreF16>(sl, x, y, z, v); break;
-            case HLBM_BF16DEV: cell_stats<StoreBF16>(sl, x, y, z, v); break;
-            default: cell_stats<StoreF32>(sl, x, y, z, v); break;
+    int xt, y, z;
+    DiagCell<float> a;
+    if (tile_cell(sl, t - sl.tile_begin, threadIdx.x, xt, y, z)) {
+        const int n = sl.pair ? 2 : 1;
+        for (int h = 0; h < n; ++h) {
+            const int x = sl.pair ? 2 * xt + h : xt;
+            switch (sl.storage) {
+                case HLBM_F16DEV: cell_stats<StoreF16>(sl, x, y, z, a); break;
+                case HLBM_BF16DEV: cell_stats<StoreBF16>(sl, x, y, z, a); break;
+                default: cell_stats<StoreF32>(sl, x, y, z, a); break;
+            }
         }
     }
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) v[c] = c >= 6 ? wmax(v[c]) : wsum(v[c]);
-    if ((tid & 31) == 0)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) sh[tid >> 5][c] = v[c];
-    __syncthreads();
-    if (tid < 8) {
-        double a = sh[0][tid];
-        for (int w = 1; w < 8; ++w) a = tid >= 6 ? fmax(a, sh[w][tid]) : a + sh[w][tid];
-        partials[(size_t)t * 8 + tid] = a;
-    }
+    diag_fold<float, 2>(a, sh, threadIdx.x, kBlock, (double)sl.ph.Fx, (double)sl.ph.Fy, (double)sl.ph.Fz,
+                        partials + (size_t)t * 8);
 }
 
 // One block per slot folds that slot's tile partials in a fixed order.
 __global__ void __launch_bounds__(256)
 k_batched_final(const DevTable* __restrict__ tab, const double* __restrict__ partials, double* __restrict__ out) {
-    __shared__ double sh[8][256];
+    __shared__ double buf[256];
     const DevSlot& sl = tab->slot[blockIdx.x];
-    const int tid = threadIdx.x;
-    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int t = tid; t < sl.ntiles; t += blockDim.x)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const double p = partials[(size_t)(sl.tile_begin + t) * 8 + c];
-            v[c] = c >= 6 ? fmax(v[c], p) : v[c] + p;
-        }
-#pragma unroll
-    for (int c = 0; c < 8; ++c) sh[c][tid] = v[c];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (tid < s)
-#pragma unroll
-            for (int c = 0; c < 8; ++c) sh[c][tid] = c >= 6 ? fmax(sh[c][tid], sh[c][tid + s]) : sh[c][tid] + sh[c][tid + s];
-        __syncthreads();
+    const double* p = partials + (size_t)sl.tile_begin * 8;
+    double v[8];
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+        v[c] = c == 5 ? 0.0 : fold_column(p, (size_t)sl.ntiles, c, buf);
+        __syncthreads();  // buf is reused by the next column
     }
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         const double cells = (double)sl.nx * sl.ny * sl.nz;
         double* o = out + (size_t)blockIdx.x * 8;
-        o[0] = cells + sh[0][0];
-        o[1] = sh[1][0];
-        o[2] = sh[2][0];
-        o[3] = sh[3][0];
-        o[4] = sh[4][0];
-        o[5] = sl.Fx64 != 0.0 ? sl.nu * (sh[1][0] / cells) / sl.Fx64 : 0.0;
-        o[6] = sh[6][0];
-        o[7] = sh[7][0];
+        o[0] = cells + v[0];
+        o[1] = v[1];
+        o[2] = v[2];
+        o[3] = v[3];
+        o[4] = v[4];
+        o[5] = sl.Fx64 != 0.0 ? sl.nu * (v[1] / cells) / sl.Fx64 : 0.0;
+        o[6] = v[6];
+        o[7] = v[7];
     }
 }
 
@@ -298,9 +362,10 @@ struct Pending {
 // admissions in a row the request fails with HLBM_ERR_OOM.
 constexpr int kMaxAllocRetries = 8;
 // A reduced-precision slot moves to FP32 once its residual is below
-// floor_coef * max|u| (or the tolerance), or has not improved by 10 % for
-// this many checks.
+// floor_coef * max|u| (or the tolerance), or its relative residual has not
+// improved by 10 % for this many checks while within kStallBand times the floor.
 constexpr int kStallChecks = 20;
+constexpr double kStallBand = 10.0;
 
 struct Live {
     Pending p;
@@ -309,9 +374,10 @@ struct Live {
     long long steps = 0;
     long long steps_low = 0;  // steps run in the reduced-precision storage
     double t_admit = 0.0;
-    double best_du = 1e300;
+    double best_du = 1e300;  // best relative residual max|du| / max|u| so far
     int stall = 0;
     bool cancel = false;
+    double credit = 1.0;  // rounds owed to the slot under the age-priority share (runs at once)
 };
 
 double feq_rest(int i) {
@@ -328,6 +394,9 @@ struct hlbm_server {
     int check_every = 100;
     int refine = 1;             // move reduced-precision slots to FP32 at their floor
     double floor_coef = 2e-3;   // reduced-precision residual floor, in units of max|u|
+    double share = 0.25;        // fraction of rounds a slot other than the oldest runs in
+    std::vector<int> run;       // live slots (indices) that run this round, in table order
+    std::vector<uint64_t> table_ids;  // request ids of the slots in the device table, in order
     size_t budget = 0, used = 0;
     cudaStream_t stream = nullptr, cap_stream = nullptr;
     int device = 0;
@@ -339,7 +408,7 @@ struct hlbm_server {
     DevTable* htab = nullptr;
     bool table_dirty = true;
     cudaGraphExec_t gexec = nullptr;
-    int grid_low = 0, grid_f32 = 0;  // blocks of the captured launches (>= the tiles they cover)
+    int grid[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // blocks of the captured launches per kernel class (>= its tiles)
     double* dpartials = nullptr;
     size_t partial_cap = 0;  // tiles
     double* dout = nullptr;
@@ -460,16 +529,9 @@ cudaError_t admit(hlbm_server_t* s, Pending& p, Live& l) {
     l.ds.nx = r.nx;
     l.ds.ny = r.ny;
     l.ds.nz = r.nz;
-    l.ds.tw_log2 = 5;
-    while (l.ds.tw_log2 < 7 && (1 << l.ds.tw_log2) < r.nx) ++l.ds.tw_log2;
-    const int tw = 1 << l.ds.tw_log2, th = kBlock / tw;
-    l.ds.tiles_x = (r.nx + tw - 1) / tw;
-    l.ds.tiles_y = (r.ny + th - 1) / th;
-    l.ds.rcp_tiles_x = 1.0f / (float)l.ds.tiles_x;
-    l.ds.rcp_tiles_y = 1.0f / (float)l.ds.tiles_y;
-    l.ds.ntiles = l.ds.tiles_x * l.ds.tiles_y * r.nz;
     l.ds.fx_only = r.F[1] == 0.0 && r.F[2] == 0.0;
     l.ds.storage = s->storage;
+    set_tiles(l.ds);
     l.ds.scale = (float)scale_of(s->storage);
     l.ds.inv_scale = (float)(1.0 / scale_of(s->storage));
     l.ds.ph = make_phys<float, 19>(r.tau, r.F);
@@ -521,6 +583,7 @@ cudaError_t widen_to_fp32(hlbm_server_t* s, Live& l) {
     l.ds.f[0] = a;
     l.ds.f[1] = b;
     l.ds.storage = HLBM_F32;
+    set_tiles(l.ds);  // per-cell tiles from now on
     l.ds.scale = 1.0f;
     l.ds.inv_scale = 1.0f;
     s->used += extra;
@@ -537,11 +600,19 @@ int build_graph(hlbm_server_t* s) {
     cudaGraph_t graph = nullptr;
     SRV_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < s->check_every; ++k) {
-        if (s->grid_low > 0 && s->storage == HLBM_F16DEV)
-            k_batched_step<StoreF16><<<s->grid_low, kBlock, 0, s->cap_stream>>>(s->dtab, k);
-        if (s->grid_low > 0 && s->storage == HLBM_BF16DEV)
-            k_batched_step<StoreBF16><<<s->grid_low, kBlock, 0, s->cap_stream>>>(s->dtab, k);
-        if (s->grid_f32 > 0) k_batched_step<StoreF32><<<s->grid_f32, kBlock, 0, s->cap_stream>>>(s->dtab, k);
+        const int* g = s->grid;
+        if (g[2 * HLBM_F16DEV + 1] > 0)
+            k_batched_step<StoreF16, true><<<g[2 * HLBM_F16DEV + 1], kBlock, 0, s->cap_stream>>>(s->dtab, k);
+        if (g[2 * HLBM_F16DEV] > 0)
+            k_batched_step<StoreF16, false><<<g[2 * HLBM_F16DEV], kBlock, 0, s->cap_stream>>>(s->dtab, k);
+        if (g[2 * HLBM_BF16DEV + 1] > 0)
+            k_batched_step<StoreBF16, true><<<g[2 * HLBM_BF16DEV + 1], kBlock, 0, s->cap_stream>>>(s->dtab, k);
+        if (g[2 * HLBM_BF16DEV] > 0)
+            k_batched_step<StoreBF16, false><<<g[2 * HLBM_BF16DEV], kBlock, 0, s->cap_stream>>>(s->dtab, k);
+        if (g[2 * HLBM_F32 + 1] > 0)
+            k_batched_step<StoreF32, true><<<g[2 * HLBM_F32 + 1], kBlock, 0, s->cap_stream>>>(s->dtab, k);
+        if (g[2 * HLBM_F32] > 0)
+            k_batched_step<StoreF32, false><<<g[2 * HLBM_F32], kBlock, 0, s->cap_stream>>>(s->dtab, k);
     }
     cudaError_t e = cudaStreamEndCapture(s->cap_stream, &graph);
     if (e != cudaSuccess) return srv_cuda_fail(e);
@@ -555,30 +626,70 @@ int build_graph(hlbm_server_t* s) {
     return HLBM_OK;
 }
 
-// Grid for `tiles` tiles: a power of two >= tiles, kept while it stays within 8x.
+// Grid for `tiles` tiles: a power of two >= tiles, kept while it stays within 8x;
+// no launch for an empty class.
 int fit_grid(int cur, int tiles) {
-    if (tiles == 0) return cur;
+    if (tiles == 0) return 0;
     if (cur >= tiles && cur <= 8 * tiles) return cur;
     int g = 256;
     while (g < tiles) g *= 2;
     return g;
 }
 
+// This round's slots. The oldest live request (lowest id) runs every round;
+// every other slot runs in a `share` fraction of the rounds (its credit grows
+// by `share` per round and a run costs 1), so the head of the queue gets most
+// of the GPU while later arrivals keep advancing: the batch approaches
+// first-come first-served for long solves without stalling short ones. The
+// policy stays work-conserving: slots are also taken in age order until a
+// round holds kRoundCells cells, so a small head never leaves the GPU idle.
+// share = 1 is plain processor sharing. Returns true when the set (or its
+// order) differs from the device table.
+constexpr double kRoundCells = 4.0e6;
+
+bool choose_run(hlbm_server_t* s) {
+    std::vector<int> age(s->live.size());
+    for (int i = 0; i < (int)age.size(); ++i) age[i] = i;
+    std::sort(age.begin(), age.end(), [s](int a, int b) { return s->live[a].p.id < s->live[b].p.id; });
+    s->run.clear();
+    double cells = 0.0;
+    for (size_t r = 0; r < age.size(); ++r) {
+        Live& l = s->live[age[r]];
+        if (r > 0) {
+            l.credit += s->share;
+            if (l.credit < 1.0 - 1e-9 && cells >= kRoundCells) continue;
+            l.credit = std::max(0.0, l.credit - 1.0);
+        }
+        s->run.push_back(age[r]);
+        cells += (double)l.ds.nx * l.ds.ny * l.ds.nz;
+    }
+    std::stable_sort(s->run.begin(), s->run.end(), [s](int a, int b) {
+        const int ca = kernel_class(s->live[a].ds), cb = kernel_class(s->live[b].ds);
+        return ca != cb ? ca < cb : s->live[a].p.id < s->live[b].p.id;
+    });
+    if (s->run.size() != s->table_ids.size()) return true;
+    for (size_t k = 0; k < s->run.size(); ++k)
+        if (s->live[s->run[k]].p.id != s->table_ids[k]) return true;
+    return false;
+}
+
 int upload_table(hlbm_server_t* s) {
-    // slots grouped by storage (each storage kernel strides over its own range);
-    // a slot's arithmetic does not depend on its position in the table
-    std::stable_sort(s->live.begin(), s->live.end(),
-                     [](const Live& a, const Live& b) { return a.ds.storage < b.ds.storage; });
+    // the running slots grouped by kernel class (each class kernel strides over its own
+    // range); a slot's arithmetic does not depend on its position in the table
     int tiles = 0;
-    s->htab->nslots = (int)s->live.size();
-    for (int st = 0; st < 4; ++st) s->htab->lo[st] = s->htab->hi[st] = 0;
-    for (size_t k = 0; k < s->live.size(); ++k) {
-        const int st = s->live[k].ds.storage;
-        if (k == 0 || s->live[k - 1].ds.storage != st) s->htab->lo[st] = tiles;
-        s->live[k].ds.tile_begin = tiles;
-        tiles += s->live[k].ds.ntiles;
-        s->htab->hi[st] = tiles;
-        s->htab->slot[k] = s->live[k].ds;
+    s->htab->nslots = (int)s->run.size();
+    s->table_ids.clear();
+    for (int c = 0; c < 8; ++c) s->htab->lo[c] = s->htab->hi[c] = 0;
+    for (size_t k = 0; k < s->run.size(); ++k) {
+        Live& l = s->live[s->run[k]];
+        const int c = kernel_class(l.ds);
+        if (k == 0 || kernel_class(s->live[s->run[k - 1]].ds) != c) s->htab->lo[c] = tiles;
+        l.ds.tile_begin = tiles;
+        s->htab->begin[k] = tiles;
+        tiles += l.ds.ntiles;
+        s->htab->hi[c] = tiles;
+        s->htab->slot[k] = l.ds;
+        s->table_ids.push_back(l.p.id);
     }
     s->htab->total_tiles = tiles;
     if ((size_t)tiles > s->partial_cap) {
@@ -589,15 +700,16 @@ int upload_table(hlbm_server_t* s) {
         SRV_CUDA(cudaMallocAsync(&s->dpartials, cap * 8 * sizeof(double), s->stream));
         s->partial_cap = cap;
     }
-    const size_t bytes = offsetof(DevTable, slot) + sizeof(DevSlot) * s->live.size();
+    const size_t bytes = offsetof(DevTable, slot) + sizeof(DevSlot) * s->run.size();
     SRV_CUDA(cudaMemcpyAsync(s->dtab, s->htab, bytes, cudaMemcpyHostToDevice, s->stream));
     s->table_dirty = false;
-    const int low = s->storage == HLBM_F32 ? 0 : s->htab->hi[s->storage] - s->htab->lo[s->storage];
-    const int f32 = s->htab->hi[HLBM_F32] - s->htab->lo[HLBM_F32];
-    const int gl = fit_grid(s->grid_low, low), gf = fit_grid(s->grid_f32, f32);
-    if (gl != s->grid_low || gf != s->grid_f32 || !s->gexec) {
-        s->grid_low = gl;
-        s->grid_f32 = gf;
+    bool rebuild = !s->gexec;
+    for (int c = 0; c < 8; ++c) {
+        const int gc = fit_grid(s->grid[c], s->htab->hi[c] - s->htab->lo[c]);
+        rebuild = rebuild || gc != s->grid[c];
+        s->grid[c] = gc;
+    }
+    if (rebuild) {
         return build_graph(s);
     }
     return HLBM_OK;
@@ -647,6 +759,13 @@ int hlbm_server_set_refinement(hlbm_server_t* s, int enable, double floor_coef) 
     std::lock_guard<std::mutex> lk(s->mu);
     s->refine = enable ? 1 : 0;
     s->floor_coef = floor_coef;
+    return HLBM_OK;
+}
+
+int hlbm_server_set_priority(hlbm_server_t* s, double share) {
+    if (!s || !(share > 0.0) || !(share <= 1.0)) return HLBM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->share = share;
     return HLBM_OK;
 }
 
@@ -741,55 +860,26 @@ int hlbm_server_pump(hlbm_server_t* s, int* active, int* waiting) {
         s->table_dirty = true;
     }
     if (!s->live.empty()) {
-        if (s->table_dirty) {
+        // 2. this round's slots, then check_every batched steps of each of them
+        if (choose_run(s) || s->table_dirty) {
             int rc = upload_table(s);
             if (rc != HLBM_OK) return rc;
         }
-        // 2. check_every batched steps of every live slot
         SRV_CUDA(cudaGraphLaunch(s->gexec, s->stream));
         // 3. per-slot FP64 diagnostics
         const int tiles = s->htab->total_tiles;
         k_batched_partials<<<tiles, kBlock, 0, s->stream>>>(s->dtab, s->dpartials);
         SRV_CUDA(cudaGetLastError());
-        const int ns = (int)s->live.size();
+        const int ns = (int)s->run.size();
         k_batched_final<<<ns, 256, 0, s->stream>>>(s->dtab, s->dpartials, s->dout);
         SRV_CUDA(cudaGetLastError());
         SRV_CUDA(cudaMemcpyAsync(s->hout, s->dout, (size_t)ns * 8 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
         SRV_CUDA(cudaStreamSynchronize(s->stream));
         s->rounds++;
         // 4. retire converged / exhausted / cancelled slots; widen slots at their floor
-        std::vector<Live> keep;
-        keep.reserve(s->live.size());
-        for (int k = 0; k < ns; ++k) {
-            Live& l = s->live[k];
-            l.steps += s->check_every;
-            if (l.ds.storage != HLBM_F32) l.steps_low += s->check_every;
-            s->lups += (long long)s->check_every * l.ds.nx * l.ds.ny * l.ds.nz;
-            const double* o = s->hout + (size_t)k * 8;
-            const bool low = l.ds.storage != HLBM_F32;
-            int status = 1;
-            if (l.cancel) status = HLBM_ERR_CANCELLED;
-            else if (o[6] < l.p.req.tol && !(low && s->refine)) status = HLBM_OK;
-            else if (l.steps >= l.p.req.max_steps) status = HLBM_ERR_NOT_CONVERGED;
-            if (status == 1 && low && s->refine) {
-                if (o[6] < 0.9 * l.best_du) {
-                    l.best_du = o[6];
-                    l.stall = 0;
-                } else {
-                    ++l.stall;
-                }
-                const bool at_floor = o[6] < std::max(l.p.req.tol, s->floor_coef * o[7]) || l.stall >= kStallChecks;
-                if (at_floor) {
-                    cudaError_t e = widen_to_fp32(s, l);
-                    if (e == cudaErrorMemoryAllocation) cudaGetLastError();  // retry at a later round
-                    else if (e != cudaSuccess) return srv_cuda_fail(e);
-                    else s->table_dirty = true;
-                }
-            }
-            if (status == 1) {
-                keep.push_back(l);
-                continue;
-            }
+        std::vector<char> gone(s->live.size(), 0);
+        auto retire = [&](int i, int status, const double* o) -> int {
+            Live& l = s->live[i];
             if (l.p.req.u_out && status != HLBM_ERR_CANCELLED) {
                 const size_t n = (size_t)l.ds.nx * l.ds.ny * l.ds.nz;
                 void* du = nullptr;
@@ -804,9 +894,61 @@ int hlbm_server_pump(hlbm_server_t* s, int* active, int* waiting) {
             finish(s, l, status, o);
             free_slot(s, l);
             cudaFreeHost(l.p.field);
+            gone[i] = 1;
             s->table_dirty = true;
+            return HLBM_OK;
+        };
+        for (int k = 0; k < ns; ++k) {
+            Live& l = s->live[s->run[k]];
+            l.steps += s->check_every;
+            if (l.ds.storage != HLBM_F32) l.steps_low += s->check_every;
+            s->lups += (long long)s->check_every * l.ds.nx * l.ds.ny * l.ds.nz;
+            const double* o = s->hout + (size_t)k * 8;
+            const bool low = l.ds.storage != HLBM_F32;
+            int status = 1;
+            if (l.cancel) status = HLBM_ERR_CANCELLED;
+            else if (o[6] < l.p.req.tol && !(low && s->refine)) status = HLBM_OK;
+            else if (l.steps >= l.p.req.max_steps) status = HLBM_ERR_NOT_CONVERGED;
+            if (status == 1 && low && s->refine) {
+                // Stall test on the relative residual max|du| / max|u|: during the start-up
+                // transient the flow accelerates almost uniformly, so max|du| over an interval
+                // stays flat while max|u| grows, and only the ratio shows the progress. A ratio
+                // that stops falling counts as a stall only near the rounding floor (within
+                // kStallBand of it).
+                const double rel = o[7] > 0.0 ? o[6] / o[7] : o[6];
+                if (rel < 0.9 * l.best_du) {
+                    l.best_du = rel;
+                    l.stall = 0;
+                } else if (rel < kStallBand * s->floor_coef) {
+                    ++l.stall;
+                } else {
+                    l.stall = 0;
+                }
+                const bool at_floor = o[6] < std::max(l.p.req.tol, s->floor_coef * o[7]) || l.stall >= kStallChecks;
+                if (at_floor) {
+                    cudaError_t e = widen_to_fp32(s, l);
+                    if (e == cudaErrorMemoryAllocation) cudaGetLastError();  // retry at a later round
+                    else if (e != cudaSuccess) return srv_cuda_fail(e);
+                    else s->table_dirty = true;
+                }
+            }
+            if (status != 1) {
+                int rc = retire(s->run[k], status, o);
+                if (rc != HLBM_OK) return rc;
+            }
         }
+        // a cancelled slot that did not run this round leaves at once
+        for (int i = 0; i < (int)s->live.size(); ++i)
+            if (!gone[i] && s->live[i].cancel) {
+                int rc = retire(i, HLBM_ERR_CANCELLED, nullptr);
+                if (rc != HLBM_OK) return rc;
+            }
+        std::vector<Live> keep;
+        keep.reserve(s->live.size());
+        for (int i = 0; i < (int)s->live.size(); ++i)
+            if (!gone[i]) keep.push_back(s->live[i]);
         s->live.swap(keep);
+        s->run.clear();  // indices into the old live list
     }
     if (active) *active = (int)s->live.size();
     if (waiting) *waiting = (int)s->waiting.size();

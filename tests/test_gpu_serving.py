@@ -196,3 +196,59 @@ def test_precision_ladder_reaches_tolerance():
     (o,) = off.run_until_idle()
     off.close()
     assert o["status"] == hb.HLBM_ERR_NOT_CONVERGED and o["final_storage"] == hb.HLBM_F16DEV
+
+
+@pytest.mark.parametrize("storage", [hb.HLBM_F16DEV, hb.HLBM_BF16DEV, hb.HLBM_F32])
+@pytest.mark.parametrize("F", [(1e-5, 0.0, 0.0), (1e-5, 2e-6, -3e-6)])
+@pytest.mark.parametrize("dims", [(32, 32, 32), (96, 40, 24), (50, 30, 20)])
+def test_batched_slot_bit_identical_to_single_lattice(dims, F, storage):
+    """A slot served without refinement holds, after 400 steps, the same velocity field bit for
+    bit as the single-lattice path in the same storage: the batched kernels (paired 16-bit
+    kernel with either load scheme, per-cell kernel) and the single-lattice kernels compute
+    the same collision. nx = 50 gives 25 pairs per row, a tile with idle lanes."""
+    nx, ny, nz = dims
+    vp = inputs.regular_sphere_field((nx, ny, nz), period=10 if nx == 50 else 8, radius_ratio=0.3)
+    srv = Server(1 << 30, storage, 100, refine=False)
+    srv.submit(vp, tau=0.6, F=F, tol=1e-30, max_steps=400, want_u=True)
+    (r,) = srv.run_until_idle()
+    srv.close()
+    assert r["status"] == hb.HLBM_ERR_NOT_CONVERGED and r["steps"] == 400
+    lat = make_lattice(19, (nz, ny, nx), storage, hb.HLBM_TWO_LATTICE, 0.6, F, (0, 0, 0), varpi=vp)
+    lat.step(400)
+    _, u = lat.moments()
+    lat.close()
+    np.testing.assert_array_equal(r["u"], u)
+
+
+@pytest.mark.parametrize("share", [1.0, 0.25])
+def test_age_priority_changes_when_not_what(share):
+    """Three equal 160^3 requests (each above the 4M cells a round is filled to) submitted
+    in order. With share = 1 every live request advances every round, so all finish in the
+    same round; with share = 0.25 the oldest advances every round and the others in a
+    quarter of the rounds, so they finish in submission order. The results themselves are
+    bit-identical in both schedules."""
+    vp = field(160, 32, 0.3)
+    srv = Server(4 << 30, hb.HLBM_F16DEV, 100, share=share)
+    ids = [srv.submit(vp, tol=1e-30, max_steps=400, want_u=True) for _ in range(3)]
+    finished_round = {}
+    rounds = 0
+    results = []
+    while True:
+        a, w = srv.pump()
+        rounds += 1
+        for r in srv.poll():
+            finished_round[r["id"]] = rounds
+            results.append(r)
+        if a == 0 and w == 0:
+            break
+    srv.close()
+    assert all(r["steps"] == 400 for r in results)
+    rs = [finished_round[i] for i in ids]
+    if share == 1.0:
+        assert rs == [4, 4, 4]
+    else:
+        assert rs == [4, 6, 8]
+    u0 = results[0]["u"]
+    for r in results[1:]:
+        np.testing.assert_array_equal(r["u"], u0)
+        assert r["k_app"] == results[0]["k_app"]
