@@ -47,6 +47,8 @@ KERNEL_TRAFFIC_BYTES = {
     # k_step<19, StoreF32, periodic, two-lattice, int, shift-fx>, 256^3: mean of two launches
     # (1342212864 + 1229032448 and 1342241536 + 1218956288 bytes)
     ("stream_collide_d3q19_f32_two", 256): 2566221568,
+    # k_step_pair<19, StoreF16, shift-fx>, 384^3: mean of two launches (read 2.378 GB + write 2.112 GB)
+    ("stream_collide_d3q19_f16_two", 384): 4490235000,
 }
 
 WORKLOADS = {

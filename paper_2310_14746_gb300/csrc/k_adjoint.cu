@@ -28,8 +28,11 @@ static Geometry geom(const LaunchCtx& c) {
     return Geometry{c.nx, c.ny, c.nz, c.wall[0], c.wall[1], c.wall[2], (size_t)c.nx * c.ny * c.nz};
 }
 
-template <int Q, class S, bool WALLS>
-__global__ void __launch_bounds__(256)
+// I: index type (int while every index of the [q][cells] arrays fits). Three
+// blocks of 256 per SM (80 registers): the kernel moves 240 B per cell and
+// needs resident warps to keep that many loads in flight.
+template <int Q, class S, bool WALLS, class I>
+__global__ void __launch_bounds__(256, 3)
 k_adjoint_step(const typename S::T* __restrict__ fn, const float* __restrict__ lam_in, float* __restrict__ lam_out,
                const float* __restrict__ varpi, float* __restrict__ grad, Geometry g, Phys<typename S::C> ph,
                typename S::C inv_s) {
@@ -39,9 +42,9 @@ k_adjoint_step(const typename S::T* __restrict__ fn, const float* __restrict__ l
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const Nbr<long long> nb(g, x, y, z);
-    const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
-    const size_t N = g.N;
+    const Nbr<I> nb(g, x, y, z);
+    const I cell = (I)x + (I)g.nx * ((I)y + (I)g.ny * (I)z);
+    const I N = (I)g.N;
 
     // forward quantities at g = S f^n
     C d[Q];
@@ -64,7 +67,7 @@ k_adjoint_step(const typename S::T* __restrict__ fn, const float* __restrict__ l
     C bux = 0, buy = 0, buz = 0, brho = 0, dvp = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        lam[i] = __ldg(lam_in + (size_t)i * N + cell);
+        lam[i] = __ldg(lam_in + (I)i * N + cell);
         const C cx = C(L::cx(i)), cy = C(L::cy(i)), cz = C(L::cz(i));
         const C w = C(L::w(i));
         const C cv = cx * vx + cy * vy + cz * vz;
@@ -95,8 +98,7 @@ k_adjoint_step(const typename S::T* __restrict__ fn, const float* __restrict__ l
         // (S^T mu)_k(y) = mu_k(y + c_k): mu_k(x) goes to y = x - c_k, or, when x - c_k
         // lies beyond a wall, to slot opp(k) of x itself.
         const bool wall = WALLS && nb.template beyond_wall<Q>(k, -1);
-        const long long dst = wall ? (long long)opp<Q>(k) * (long long)N + cell
-                                   : (long long)k * (long long)N + cell + nb.template offset<Q>(k, -1);
+        const I dst = wall ? (I)opp<Q>(k) * N + cell : (I)k * N + cell + nb.template offset<Q>(k, -1);
         lam_out[dst] = float(mu);
     }
 }
@@ -165,8 +167,13 @@ static cudaError_t adjoint_impl(const LaunchCtx& c, const void* fn, const float*
     const Phys<C> ph = make_phys<C, Q>(c.tau, c.F);
     const dim3 blk = block_for(c.nx);
     const dim3 grd((c.nx + blk.x - 1) / blk.x, (c.ny + blk.y - 1) / blk.y, c.nz);
-    k_adjoint_step<Q, S, WALLS><<<grd, blk, 0, c.stream>>>(static_cast<const typename S::T*>(fn), lam_in, lam_out,
-                                                           varpi, grad, g, ph, C(1.0 / c.scale));
+    const auto* f = static_cast<const typename S::T*>(fn);
+    if ((size_t)Q * g.N < ((size_t)1 << 31))
+        k_adjoint_step<Q, S, WALLS, int><<<grd, blk, 0, c.stream>>>(f, lam_in, lam_out, varpi, grad, g, ph,
+                                                                    C(1.0 / c.scale));
+    else
+        k_adjoint_step<Q, S, WALLS, long long><<<grd, blk, 0, c.stream>>>(f, lam_in, lam_out, varpi, grad, g, ph,
+                                                                          C(1.0 / c.scale));
     return cudaGetLastError();
 }
 
