@@ -320,7 +320,7 @@ typedef struct {
  * floor, is converted in place to FP32 storage (when the budget allows) and
  * must then meet its tolerance in FP32. Scheduling: every round the oldest
  * live request advances check_every steps; the other live requests advance
- * in a `share` of the rounds (default 0.25; hlbm_server_set_priority). */
+ * in a `share` of the rounds (default 0.1; hlbm_server_set_priority). */
 int hlbm_server_create(hlbm_server_t** out, size_t mem_budget, int storage, int check_every,
                        void* cuda_stream);
 /* Turn refinement on or off and set its floor coefficient (>= 0). With it off,

@@ -394,7 +394,7 @@ struct hlbm_server {
     int check_every = 100;
     int refine = 1;             // move reduced-precision slots to FP32 at their floor
     double floor_coef = 2e-3;   // reduced-precision residual floor, in units of max|u|
-    double share = 0.25;        // fraction of rounds a slot other than the oldest runs in
+    double share = 0.1;         // fraction of rounds a slot other than the oldest runs in
     std::vector<int> run;       // live slots (indices) that run this round, in table order
     std::vector<uint64_t> table_ids;  // request ids of the slots in the device table, in order
     size_t budget = 0, used = 0;
