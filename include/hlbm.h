@@ -370,8 +370,9 @@ void hlbm_server_destroy(hlbm_server_t* s);
  * memory the library allocates: its scratch is a fixed 4 MiB array in the
  * library's device memory, which every GPU that loads the library keeps
  * until the process exits. A lattice whose reduction needs more than 65536
- * partial blocks (blocks of 256 threads over x-rows of up to 128 cells; 256^3
- * is the largest cube that fits) returns HLBM_ERR_SCRATCH_LIMIT. The first
+ * partial blocks (blocks of 256 threads over x-rows of up to 128 cells and
+ * four z planes; 384^3 is the largest cube that fits) returns
+ * HLBM_ERR_SCRATCH_LIMIT. The first
  * call on a device looks up the array's device address (once per device);
  * make that first call before any stream capture. Every call on a device
  * shares the array: calls whose work overlaps on the same GPU race on it, so

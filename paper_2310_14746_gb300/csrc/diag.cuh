@@ -3,18 +3,21 @@
 // reduction kernels.
 //
 // GB300 runs FP64 arithmetic (and float<->double conversion) at a small
-// fraction of its FP32 rate, so the fold keeps FP64 work to what the sums
-// need:
-//  * each thread converts its cell's drho and j to double (4 conversions);
-//    the F/2 shift of rho*u is added once per block from the count of fluid
-//    cells instead of once per cell (shift form only);
-//  * the residual max|du| and the speed max|u| stay in the arithmetic type:
-//    a max is exact in any precision and order-independent, and is folded on
-//    the bit patterns (non-negative values order like unsigned integers), so
-//    a NaN anywhere reaches the result instead of being dropped by fmax;
-//  * the five sums are folded through shared memory in a fixed order (40
-//    threads sum interleaved segments, 5 threads combine them), not with
-//    shuffle trees: the result does not depend on scheduling.
+// fraction of its FP32 rate, and a fold built from long dependent chains of
+// FP64 adds is latency-bound. So:
+//  * a thread first adds its own few cells (at most four) in the arithmetic
+//    type; the rounding of that short sum is far below the FP32 rounding of
+//    each cell's own moments, and every sum beyond the thread is FP64;
+//  * the F/2 shift of rho*u is added once per block from the exact count of
+//    fluid cells instead of once per cell (shift form only);
+//  * max|du| and max|u| stay in the arithmetic type: a max is exact in any
+//    precision and order-free, and is folded on the bit patterns
+//    (non-negative values order like unsigned integers), so a NaN anywhere
+//    reaches the result instead of being dropped by fmax;
+//  * the five sums are folded through shared memory by one warp per
+//    quantity: each lane adds a fixed strided set, then a fixed shuffle tree
+//    (dependency depth nt/32 - 1 + 5 instead of a 38-long chain). The result
+//    does not depend on scheduling.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -50,70 +53,65 @@ __device__ __forceinline__ C nan_max(C a, C b) {
     return (b > a || b != b) ? b : a;
 }
 
-// One thread's diagnostics over its cells (one or two). s[0] = sum drho,
-// s[1..3] = sum j (plus F/2 and the drag factor when `shifted` is set), s[4]
-// = the part of s[1] on the x = nx-1 plane; fluid / plane count the cells
-// behind s[1..3] / s[4].
+// One thread's diagnostics over its cells. p[0] = sum drho, p[1..3] = sum j
+// (plus F/2 and the drag factor when `shifted` is set), p[4] = the part of
+// p[1] on the x = nx-1 plane, all in the arithmetic type; fluid / plane count
+// the cells behind p[1..3] / p[4].
 template <class C>
 struct DiagCell {
-    double s[5] = {0, 0, 0, 0, 0};
+    C p[5] = {C(0), C(0), C(0), C(0), C(0)};
     C du = C(0), um = C(0);
     int fluid = 0, plane = 0;
-    bool shifted = false;  // F/2 already inside s[1..4]
+    bool shifted = false;  // F/2 already inside p[1..4]
 };
 
-constexpr int kDiagPad = 264;  // row stride of the fold buffer (conflict-free 64-bit reads)
-
 struct DiagShared {
-    double sum[5][kDiagPad];
-    double seg[5][8];
+    double sum[5][256];
     unsigned long long mx[2];
+    int cnt[2];
 };
 
 // Fold the block's cells into out[8] (drho sum, rho*u sum (3), plane flux, 0,
 // max|du|, max|u|). Every thread of the block calls it; nt = threads (a
-// multiple of 8, at most 256), F = the force in double, MAXC = the most
-// cells a thread holds.
-template <class C, int MAXC = 1>
+// multiple of 32, from 192 to 256), F = the force in double.
+template <class C>
 __device__ __forceinline__ void diag_fold(const DiagCell<C>& a, DiagShared& sh, int t, int nt, double Fx, double Fy,
                                           double Fz, double* out) {
     using B = DiagBits<C>;
-    if (t < 2) sh.mx[t] = 0ull;
+    if (t < 2) {
+        sh.mx[t] = 0ull;
+        sh.cnt[t] = 0;
+    }
 #pragma unroll
-    for (int k = 0; k < 5; ++k) sh.sum[k][t] = a.s[k];
+    for (int k = 0; k < 5; ++k) sh.sum[k][t] = (double)a.p[k];
     __syncthreads();
     const typename B::U bdu = B::warp_max(B::bits(a.du));
     const typename B::U bum = B::warp_max(B::bits(a.um));
-    if ((t & 31) == 0) {
+    const int nf = __reduce_add_sync(0xffffffffu, a.shifted ? 0 : a.fluid);
+    const int np = __reduce_add_sync(0xffffffffu, a.shifted ? 0 : a.plane);
+    const int lane = t & 31, warp = t >> 5;
+    if (lane == 0) {
         atomicMax(reinterpret_cast<typename B::U*>(&sh.mx[0]), bdu);
         atomicMax(reinterpret_cast<typename B::U*>(&sh.mx[1]), bum);
-    }
-    // the counts are exact integers; the barriers also publish sum[] and mx[]
-    int nfluid = 0, nplane = 0;
-#pragma unroll
-    for (int c = 1; c <= MAXC; ++c) {
-        nfluid += __syncthreads_count(!a.shifted && a.fluid >= c);
-        nplane += __syncthreads_count(!a.shifted && a.plane >= c);
-    }
-    if (t < 40) {
-        const int k = t >> 3, sg = t & 7, per = nt >> 3;
-        double v = sh.sum[k][sg];
-        for (int m = 1; m < per; ++m) v += sh.sum[k][m * 8 + sg];
-        sh.seg[k][sg] = v;
+        atomicAdd(&sh.cnt[0], nf);  // integers: exact in any order
+        atomicAdd(&sh.cnt[1], np);
     }
     __syncthreads();
-    if (t < 8) {
-        double v = 0.0;
-        if (t < 5) {
-            v = sh.seg[t][0];
+    if (warp < 5) {
+        const int k = warp;
+        double v = sh.sum[k][lane];
+        for (int m = 32 + lane; m < nt; m += 32) v += sh.sum[k][m];
 #pragma unroll
-            for (int m = 1; m < 8; ++m) v += sh.seg[t][m];
-            const double half = 0.5 * (t == 1 || t == 4 ? Fx : t == 2 ? Fy : t == 3 ? Fz : 0.0);
-            if (t > 0) v += half * (double)(t == 4 ? nplane : nfluid);
-        } else if (t >= 6) {
-            v = B::value(*reinterpret_cast<const typename B::U*>(&sh.mx[t - 6]));
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+            const double half = 0.5 * (k == 1 || k == 4 ? Fx : k == 2 ? Fy : k == 3 ? Fz : 0.0);
+            if (k > 0) v += half * (double)(k == 4 ? sh.cnt[1] : sh.cnt[0]);
+            out[k] = v;
         }
-        out[t] = v;
+    } else if (warp == 5 && lane == 0) {
+        out[5] = 0.0;
+        out[6] = B::value(*reinterpret_cast<const typename B::U*>(&sh.mx[0]));
+        out[7] = B::value(*reinterpret_cast<const typename B::U*>(&sh.mx[1]));
     }
 }
 

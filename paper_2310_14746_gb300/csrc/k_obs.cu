@@ -1,5 +1,7 @@
 // Observables and state I/O: moments, FP64 diagnostics, population
 // conversion, input validation.
+#include <type_traits>
+
 #include "internal.h"
 #include "lattice.cuh"
 #include "diag.cuh"
@@ -74,61 +76,83 @@ static cudaError_t moments_impl(const LaunchCtx& c, int lay, const void* f, void
 }
 
 // ---------------------------------------------------------------------------
-// FP64 diagnostics. Stage 1: each block folds its cells into 8 doubles
-// (sum drho, sum rho*u (3), plane flux, 0, max|du|, max|u|) in a fixed order
-// (diag.cuh). Stage 2: one block per column folds the block rows in a fixed
-// order. The result does not depend on scheduling.
+// FP64 diagnostics. Stage 1: each block folds its cells (256 threads over x
+// rows, kReduceZ z planes per thread) into 8 doubles (sum drho, sum rho*u
+// (3), plane flux, 0, max|du|, max|u|) in a fixed order (diag.cuh). Stage 2:
+// one block per column folds the block rows in a fixed order. The result does
+// not depend on scheduling.
+//
+// The first version (64-bit indices, the layout chosen per direction at run
+// time, residual reference loads ordered behind the previous component's
+// store, one cell per thread) was latency-bound at 0.87 TB/s; 32-bit indices
+// with the two-lattice layout fixed at compile time and all loads issued
+// before any store bring the cell work to the copy bandwidth.
 // ---------------------------------------------------------------------------
-template <int Q, class S, bool WALLS>
+constexpr int kReduceZ = 4;
+
+template <int Q, class S, bool WALLS, bool FAST>
 __global__ void __launch_bounds__(256)
-k_reduce_partials(const typename S::T* f, int lay, Geometry g, Phys<typename S::C> ph,
-                  typename S::C inv_s, typename S::C* u_prev, int update_prev, double* partials, const float* varpi,
-                  int drag, const unsigned* links) {
+k_reduce_partials(const typename S::T* __restrict__ f, int lay, Geometry g, Phys<typename S::C> ph,
+                  typename S::C inv_s, typename S::C* __restrict__ u_prev, int update_prev,
+                  double* __restrict__ partials, const float* __restrict__ varpi, int drag,
+                  const unsigned* __restrict__ links) {
     using C = typename S::C;
+    using I = typename std::conditional<FAST, int, long long>::type;  // FAST: 32-bit indices, natural layout
     __shared__ DiagShared sh;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
     DiagCell<C> a;
-    const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
-    const unsigned lm = (links && x < g.nx && y < g.ny) ? links[cell] : 0u;
-    if (x < g.nx && y < g.ny && (lm & kSolidBit)) {
-        // resolved obstacle: rho = 1, u = 0 (contributes nothing but its residual reference)
-        if (update_prev)
-            for (int k = 0; k < 3; ++k) u_prev[k * g.N + cell] = C(0);
-    } else if (x < g.nx && y < g.ny) {
-        const Nbr<long long> nb(g, x, y, z, lm);
-        C d[Q];
+    a.shifted = drag != 0;
+    if (x < g.nx && y < g.ny) {
+        const I N = (I)g.N;
+        const int z0 = blockIdx.z * kReduceZ;
+        const int z1 = z0 + kReduceZ < g.nz ? z0 + kReduceZ : g.nz;
+        for (int z = z0; z < z1; ++z) {
+            const I cell = (I)x + (I)g.nx * ((I)y + (I)g.ny * (I)z);
+            const unsigned lm = links ? links[cell] : 0u;
+            if (lm & kSolidBit) {
+                // resolved obstacle: rho = 1, u = 0 (contributes nothing but its residual reference)
+                if (update_prev)
+                    for (int k = 0; k < 3; ++k) u_prev[(I)k * N + cell] = C(0);
+                continue;
+            }
+            const Nbr<I> nb(g, x, y, z, lm);
+            C d[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) d[i] = S::load(f, gather_index<Q, WALLS>(g, nb, cell, i, lay), inv_s);
-        C drho, jx, jy, jz;
-        moments<Q, C>(d, drho, jx, jy, jz);
-        C u3[3];
-        const C vp = drag ? C(varpi[cell]) : C(1);
-        velocity_form<C>(jx, jy, jz, C(1) + drho, vp, drag, ph, u3[0], u3[1], u3[2]);
-        a.fluid = 1;
-        a.plane = x == g.nx - 1;
-        a.s[0] = (double)drho;
-        if (drag) {
-            // rho*u = (j + F/2) / (1 + lam/2), formed in FP64 per cell
-            const double hd = 1.0 / (1.0 + 0.5 * (1.0 - (double)vp) * (double)ph.omega);
-            a.shifted = true;
-            a.s[1] = ((double)jx + 0.5 * (double)ph.Fx) * hd;
-            a.s[2] = ((double)jy + 0.5 * (double)ph.Fy) * hd;
-            a.s[3] = ((double)jz + 0.5 * (double)ph.Fz) * hd;
-        } else {
-            // rho*u = j + F/2: the F/2 is added per block from the fluid-cell count
-            a.s[1] = (double)jx;
-            a.s[2] = (double)jy;
-            a.s[3] = (double)jz;
-        }
-        if (a.plane) a.s[4] = a.s[1];
+            for (int i = 0; i < Q; ++i)
+                d[i] = S::load(f, gather_index<Q, WALLS>(g, nb, cell, i, FAST ? (int)NATURAL : lay), inv_s);
+            C up[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const C up = u_prev[k * g.N + cell];
-            a.du = nan_max(a.du, C(fabs(u3[k] - up)));
-            a.um = nan_max(a.um, C(fabs(u3[k])));
-            if (update_prev) u_prev[k * g.N + cell] = u3[k];
+            for (int k = 0; k < 3; ++k) up[k] = u_prev[(I)k * N + cell];
+            C drho, jx, jy, jz;
+            moments<Q, C>(d, drho, jx, jy, jz);
+            C u3[3];
+            const C vp = drag ? C(varpi[cell]) : C(1);
+            velocity_form<C>(jx, jy, jz, C(1) + drho, vp, drag, ph, u3[0], u3[1], u3[2]);
+            a.fluid += 1;
+            a.p[0] += drho;
+            C mx = jx, my = jy, mz = jz;
+            if (drag) {  // rho*u = (j + F/2) / (1 + lam/2)
+                const C hd = C(1) / fma_(C(0.5), (C(1) - vp) * ph.omega, C(1));
+                mx = fma_(C(0.5), ph.Fx, jx) * hd;
+                my = fma_(C(0.5), ph.Fy, jy) * hd;
+                mz = fma_(C(0.5), ph.Fz, jz) * hd;
+            }  // else rho*u = j + F/2, the F/2 added per block from the fluid-cell count
+            a.p[1] += mx;
+            a.p[2] += my;
+            a.p[3] += mz;
+            if (x == g.nx - 1) {
+                a.plane += 1;
+                a.p[4] += mx;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                a.du = nan_max(a.du, C(fabs(u3[k] - up[k])));
+                a.um = nan_max(a.um, C(fabs(u3[k])));
+            }
+            if (update_prev)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) u_prev[(I)k * N + cell] = u3[k];
         }
     }
     const size_t b = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
@@ -157,7 +181,7 @@ k_reduce_final(const double* partials, size_t nblocks, double cells, double nu, 
 
 size_t reduce_partials_count(const LaunchCtx& c) {
     const dim3 blk = block_for(c.nx);
-    return (size_t)((c.nx + blk.x - 1) / blk.x) * ((c.ny + blk.y - 1) / blk.y) * c.nz;
+    return (size_t)((c.nx + blk.x - 1) / blk.x) * ((c.ny + blk.y - 1) / blk.y) * ((c.nz + kReduceZ - 1) / kReduceZ);
 }
 
 template <int Q, class S, bool WALLS>
@@ -166,11 +190,15 @@ static cudaError_t reduce_impl(const LaunchCtx& c, int lay, const void* f, void*
     using C = typename S::C;
     const Geometry g = geom(c);
     const dim3 blk = block_for(c.nx);
-    const dim3 grd((c.nx + blk.x - 1) / blk.x, (c.ny + blk.y - 1) / blk.y, c.nz);
-    k_reduce_partials<Q, S, WALLS><<<grd, blk, 0, c.stream>>>(static_cast<const typename S::T*>(f), lay, g,
-                                                              phys<C, Q>(c), C(1.0 / c.scale),
-                                                              static_cast<C*>(u_prev), upd, partials, c.varpi,
-                                                              c.drag, c.links);
+    const dim3 grd((c.nx + blk.x - 1) / blk.x, (c.ny + blk.y - 1) / blk.y, (c.nz + kReduceZ - 1) / kReduceZ);
+    const auto* fs = static_cast<const typename S::T*>(f);
+    C* up = static_cast<C*>(u_prev);
+    if (lay == NATURAL && (size_t)Q * g.N < ((size_t)1 << 31))
+        k_reduce_partials<Q, S, WALLS, true><<<grd, blk, 0, c.stream>>>(fs, lay, g, phys<C, Q>(c), C(1.0 / c.scale),
+                                                                        up, upd, partials, c.varpi, c.drag, c.links);
+    else
+        k_reduce_partials<Q, S, WALLS, false><<<grd, blk, 0, c.stream>>>(fs, lay, g, phys<C, Q>(c), C(1.0 / c.scale),
+                                                                         up, upd, partials, c.varpi, c.drag, c.links);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_final<<<8, 256, 0, c.stream>>>(partials, reduce_partials_count(c), (double)g.N,

@@ -254,21 +254,26 @@ __device__ __forceinline__ void cell_stats(const DevSlot& sl, int x, int y, int 
     moments<19, C>(d, drho, jx, jy, jz);
     C u3[3];
     velocity<C>(jx, jy, jz, C(1) / (C(1) + drho), ph, u3[0], u3[1], u3[2]);
+    C up[3];
+    const int N = (int)g.N;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) up[c] = sl.u_prev[c * N + cell];
     a.fluid += 1;
-    a.s[0] += (double)drho;  // rho*u = j + F/2: F/2 is added per block from the counts
-    a.s[1] += (double)jx;
-    a.s[2] += (double)jy;
-    a.s[3] += (double)jz;
+    a.p[0] += drho;  // rho*u = j + F/2: F/2 is added per block from the counts
+    a.p[1] += jx;
+    a.p[2] += jy;
+    a.p[3] += jz;
     if (x == g.nx - 1) {
         a.plane += 1;
-        a.s[4] += (double)jx;
+        a.p[4] += jx;
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        a.du = nan_max(a.du, fabsf(u3[c] - sl.u_prev[c * g.N + cell]));
+        a.du = nan_max(a.du, fabsf(u3[c] - up[c]));
         a.um = nan_max(a.um, fabsf(u3[c]));
-        sl.u_prev[c * g.N + cell] = u3[c];
     }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sl.u_prev[c * N + cell] = u3[c];
 }
 
 // Per-tile FP64 partials of the diagnostics (one block per tile of any slot,
@@ -292,7 +297,7 @@ k_batched_partials(const DevTable* __restrict__ tab, double* __restrict__ partia
             }
         }
     }
-    diag_fold<float, 2>(a, sh, threadIdx.x, kBlock, (double)sl.ph.Fx, (double)sl.ph.Fy, (double)sl.ph.Fz,
+    diag_fold<float>(a, sh, threadIdx.x, kBlock, (double)sl.ph.Fx, (double)sl.ph.Fy, (double)sl.ph.Fz,
                         partials + (size_t)t * 8);
 }
 

@@ -61,7 +61,8 @@ def test_noalloc_rejects_lattice_beyond_scratch():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     small = torch.zeros(16, dtype=torch.float32, device="cuda")
-    # 32-cell rows use blocks of 32 x 8 cells: 8 x 8 x 65537 cells need 65537 partial blocks
+    # 32-cell rows use blocks of 32 x 8 cells over 4 z planes: 32 x 8 x 262145 cells need
+    # 65537 partial blocks, one more than the scratch holds (refused before any launch)
     with pytest.raises(hb.HlbmError) as e:
-        hb.hlbm_reduce_noalloc(19, 32, 8, 65537, hb.HLBM_F32, [0, 0, 0], 0.6, (0, 0, 0), 1.0, small, small)
+        hb.hlbm_reduce_noalloc(19, 32, 8, 4 * 65536 + 1, hb.HLBM_F32, [0, 0, 0], 0.6, (0, 0, 0), 1.0, small, small)
     assert e.value.status == hb.HLBM_ERR_SCRATCH_LIMIT
