@@ -330,14 +330,16 @@ int hlbm_server_set_refinement(hlbm_server_t* s, int enable, double floor_coef);
 /* Age priority of the batch (no counterpart in the paper: a serving policy).
  * share in (0, 1] is the fraction of rounds in which a live request other
  * than the oldest one advances; 1 advances every live request every round
- * (plain processor sharing). Results do not depend on it, only when they
- * arrive. */
+ * (plain processor sharing). Regardless of the share, a round takes live
+ * requests in age order until it holds at least 4M cells, so the GPU is not
+ * left idle behind a small oldest request. Results do not depend on it, only
+ * when they arrive. */
 int hlbm_server_set_priority(hlbm_server_t* s, double share);
 /* Queue a request (validated and copied); *id receives its identifier.
  * HLBM_ERR_OOM if it could never fit the budget. */
 int hlbm_server_submit(hlbm_server_t* s, const hlbm_request* r, uint64_t* id);
-/* One scheduling round: admit, run check_every steps of all live slots,
- * check, retire. Synchronises. *active / *waiting (may be NULL) receive the
+/* One scheduling round: admit, run check_every steps of this round's slots
+ * (see hlbm_server_set_priority), check them, retire. Synchronises. *active / *waiting (may be NULL) receive the
  * counts after the round. A round with no live slot launches nothing. */
 int hlbm_server_pump(hlbm_server_t* s, int* active, int* waiting);
 /* Move up to max finished results into out; *n receives how many. */
