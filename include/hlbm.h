@@ -319,8 +319,8 @@ typedef struct {
  * 1.6e-2 for BF16), or stops improving for 20 checks within 10 times that
  * floor, is converted in place to FP32 storage (when the budget allows) and
  * must then meet its tolerance in FP32. Scheduling: every round the oldest
- * live request advances check_every steps; the other live requests advance
- * in a `share` of the rounds (default 0.1; hlbm_server_set_priority). */
+ * live request advances check_every steps, and younger ones join it in age
+ * order within a cell budget (hlbm_server_set_priority). */
 int hlbm_server_create(hlbm_server_t** out, size_t mem_budget, int storage, int check_every,
                        void* cuda_stream);
 /* Turn refinement on or off and set its floor coefficient (>= 0). With it off,
@@ -328,13 +328,14 @@ int hlbm_server_create(hlbm_server_t** out, size_t mem_budget, int storage, int 
  * below the tolerance. */
 int hlbm_server_set_refinement(hlbm_server_t* s, int enable, double floor_coef);
 /* Age priority of the batch (no counterpart in the paper: a serving policy).
- * share in (0, 1] is the fraction of rounds in which a live request other
- * than the oldest one advances; 1 advances every live request every round
- * (plain processor sharing). Regardless of the share, a round takes live
- * requests in age order until it holds at least 4M cells, so the GPU is not
- * left idle behind a small oldest request. Results do not depend on it, only
- * when they arrive. */
-int hlbm_server_set_priority(hlbm_server_t* s, double share);
+ * Each round runs the oldest live request and, in age order, the younger
+ * ones that fit a budget of max(4M, (1 + backfill) * the oldest request's
+ * cells) cells; a younger request that does not fit is skipped for that
+ * round, so smaller ones behind it can still run. backfill >= 0 (default
+ * 0.25) bounds how much the oldest request is slowed by the batch, whatever
+ * the queue length; a very large value is plain processor sharing. Results
+ * do not depend on it, only when they arrive. */
+int hlbm_server_set_priority(hlbm_server_t* s, double backfill);
 /* Queue a request (validated and copied); *id receives its identifier.
  * HLBM_ERR_OOM if it could never fit the budget. */
 int hlbm_server_submit(hlbm_server_t* s, const hlbm_request* r, uint64_t* id);

@@ -369,8 +369,8 @@ def hlbm_server_create(mem_budget, storage=HLBM_F16DEV, check_every=100, stream=
     return h.value
 
 
-def hlbm_server_set_priority(s, share):
-    _check(_lib().hlbm_server_set_priority(s, float(share)), "hlbm_server_set_priority")
+def hlbm_server_set_priority(s, backfill):
+    _check(_lib().hlbm_server_set_priority(s, float(backfill)), "hlbm_server_set_priority")
 
 
 def hlbm_server_set_refinement(s, enable, floor_coef):

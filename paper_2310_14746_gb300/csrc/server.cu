@@ -382,7 +382,6 @@ struct Live {
     double best_du = 1e300;  // best relative residual max|du| / max|u| so far
     int stall = 0;
     bool cancel = false;
-    double credit = 1.0;  // rounds owed to the slot under the age-priority share (runs at once)
 };
 
 double feq_rest(int i) {
@@ -399,7 +398,7 @@ struct hlbm_server {
     int check_every = 100;
     int refine = 1;             // move reduced-precision slots to FP32 at their floor
     double floor_coef = 2e-3;   // reduced-precision residual floor, in units of max|u|
-    double share = 0.1;         // fraction of rounds a slot other than the oldest runs in
+    double backfill = 0.25;     // cells younger requests may add to a round, per cell of the oldest
     std::vector<int> run;       // live slots (indices) that run this round, in table order
     std::vector<uint64_t> table_ids;  // request ids of the slots in the device table, in order
     size_t budget = 0, used = 0;
@@ -642,14 +641,16 @@ int fit_grid(int cur, int tiles) {
 }
 
 // This round's slots. The oldest live request (lowest id) runs every round;
-// every other slot runs in a `share` fraction of the rounds (its credit grows
-// by `share` per round and a run costs 1), so the head of the queue gets most
-// of the GPU while later arrivals keep advancing: the batch approaches
-// first-come first-served for long solves without stalling short ones. The
-// policy stays work-conserving: slots are also taken in age order until a
-// round holds kRoundCells cells, so a small head never leaves the GPU idle.
-// share = 1 is plain processor sharing. Returns true when the set (or its
-// order) differs from the device table.
+// younger slots are added in age order (skipping those that do not fit, so a
+// small request can pass a large one) while the round stays within a cell
+// budget of max(kRoundCells, (1 + backfill) * the oldest request's cells).
+// The oldest request therefore never runs slower than 1 / (1 + backfill) of
+// its speed alone, however long the queue behind it: the batch approaches
+// first-come first-served for long solves (which bounds the tail) while short
+// requests fill the rest of each round. kRoundCells keeps a small oldest
+// request from leaving the GPU idle. A very large backfill is plain processor
+// sharing. Returns true when the set (or its order) differs from the device
+// table.
 constexpr double kRoundCells = 4.0e6;
 
 bool choose_run(hlbm_server_t* s) {
@@ -657,16 +658,17 @@ bool choose_run(hlbm_server_t* s) {
     for (int i = 0; i < (int)age.size(); ++i) age[i] = i;
     std::sort(age.begin(), age.end(), [s](int a, int b) { return s->live[a].p.id < s->live[b].p.id; });
     s->run.clear();
-    double cells = 0.0;
+    double cells = 0.0, budget = 0.0;
     for (size_t r = 0; r < age.size(); ++r) {
-        Live& l = s->live[age[r]];
-        if (r > 0) {
-            l.credit += s->share;
-            if (l.credit < 1.0 - 1e-9 && cells >= kRoundCells) continue;
-            l.credit = std::max(0.0, l.credit - 1.0);
+        const Live& l = s->live[age[r]];
+        const double n = (double)l.ds.nx * l.ds.ny * l.ds.nz;
+        if (r == 0) {
+            budget = std::max(kRoundCells, (1.0 + s->backfill) * n);
+        } else if (cells + n > budget) {
+            continue;
         }
         s->run.push_back(age[r]);
-        cells += (double)l.ds.nx * l.ds.ny * l.ds.nz;
+        cells += n;
     }
     std::stable_sort(s->run.begin(), s->run.end(), [s](int a, int b) {
         const int ca = kernel_class(s->live[a].ds), cb = kernel_class(s->live[b].ds);
@@ -767,10 +769,10 @@ int hlbm_server_set_refinement(hlbm_server_t* s, int enable, double floor_coef) 
     return HLBM_OK;
 }
 
-int hlbm_server_set_priority(hlbm_server_t* s, double share) {
-    if (!s || !(share > 0.0) || !(share <= 1.0)) return HLBM_ERR_INVALID_ARG;
+int hlbm_server_set_priority(hlbm_server_t* s, double backfill) {
+    if (!s || !(backfill >= 0.0) || !std::isfinite(backfill)) return HLBM_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
-    s->share = share;
+    s->backfill = backfill;
     return HLBM_OK;
 }
 

@@ -22,10 +22,10 @@ from . import (HLBM_F16DEV, HLBM_F32, HLBM_D3Q19, HLBM_TWO_LATTICE, Lattice, hlb
 
 class Server:
     def __init__(self, mem_budget=32 << 30, storage=HLBM_F16DEV, check_every=100, stream=None, refine=None,
-                 floor_coef=None, share=None):
+                 floor_coef=None, backfill=None):
         self.s = hlbm_server_create(mem_budget, storage, check_every, stream)
-        if share is not None:
-            hlbm_server_set_priority(self.s, share)
+        if backfill is not None:
+            hlbm_server_set_priority(self.s, backfill)
         self._keep = {}  # id -> (field, u_out) kept alive until polled
         if refine is not None or floor_coef is not None:
             default = 1.6e-2 if storage == 3 else 2e-3

@@ -220,34 +220,30 @@ def test_batched_slot_bit_identical_to_single_lattice(dims, F, storage):
     np.testing.assert_array_equal(r["u"], u)
 
 
-@pytest.mark.parametrize("share", [1.0, 0.25])
-def test_age_priority_changes_when_not_what(share):
-    """Three equal 160^3 requests (each above the 4M cells a round is filled to) submitted
-    in order. With share = 1 every live request advances every round, so all finish in the
-    same round; with share = 0.25 the oldest advances every round and the others in a
-    quarter of the rounds, so they finish in submission order. The results themselves are
-    bit-identical in both schedules."""
+@pytest.mark.parametrize("backfill,rounds", [(1e9, [4, 4, 4]), (1.0, [4, 4, 8]), (0.0, [4, 8, 12])])
+def test_age_priority_changes_when_not_what(backfill, rounds):
+    """Three equal 160^3 requests (4.1M cells each, above the 4M cells a round is always
+    filled to) submitted in order, 400 steps each. A round runs the oldest request plus
+    younger ones within (1 + backfill) times its cells: everything at once for a huge
+    backfill, two at a time for 1, strictly one after another for 0. The results are
+    bit-identical in every schedule."""
     vp = field(160, 32, 0.3)
-    srv = Server(4 << 30, hb.HLBM_F16DEV, 100, share=share)
+    srv = Server(4 << 30, hb.HLBM_F16DEV, 100, backfill=backfill)
     ids = [srv.submit(vp, tol=1e-30, max_steps=400, want_u=True) for _ in range(3)]
     finished_round = {}
-    rounds = 0
+    n = 0
     results = []
     while True:
         a, w = srv.pump()
-        rounds += 1
+        n += 1
         for r in srv.poll():
-            finished_round[r["id"]] = rounds
+            finished_round[r["id"]] = n
             results.append(r)
         if a == 0 and w == 0:
             break
     srv.close()
     assert all(r["steps"] == 400 for r in results)
-    rs = [finished_round[i] for i in ids]
-    if share == 1.0:
-        assert rs == [4, 4, 4]
-    else:
-        assert rs == [4, 6, 8]
+    assert [finished_round[i] for i in ids] == rounds
     u0 = results[0]["u"]
     for r in results[1:]:
         np.testing.assert_array_equal(r["u"], u0)
