@@ -3,17 +3,18 @@
 //
 // Each admitted request owns a slot: two population buffers (two-lattice
 // streaming), its porosity field, and its residual reference velocity. A
-// device slot table lists the live slots with their tile ranges and storage
-// type; one launch of the batched kernel advances every slot by one time
-// step, its blocks striding over all tiles of all slots (a tile never mixes
-// slots, so the storage branch is uniform per block). check_every launches
-// are captured once in a CUDA graph that reads the table from device memory,
-// so admissions, retirements and precision changes only rewrite the table.
-// After each graph replay a per-slot FP64 reduction (a fixed partition per
-// slot, so a slot's result does not depend on its neighbours in the batch)
-// gives the residual and the apparent permeability; converged slots retire
-// and free their memory, and waiting requests are admitted first-come
-// first-served while they fit the memory budget.
+// device slot table lists the slots of the current round with their tile
+// ranges, grouped by kernel class (storage and collision form); one launch
+// per class advances every listed slot by one time step, one block per tile
+// (a tile never mixes slots). check_every launches are captured once in a
+// CUDA graph that reads the table from device memory, so admissions,
+// retirements, precision changes and the round's slot set only rewrite the
+// table. After each graph replay a per-slot FP64 reduction (a fixed partition
+// per slot, so a slot's result does not depend on its neighbours in the
+// batch) gives the residual and the apparent permeability; converged slots
+// retire and free their memory, and waiting requests are admitted first-come
+// first-served while they fit the memory budget. Each round runs the oldest
+// live request and younger ones within a cell budget (choose_run).
 //
 // Precision ladder. With FP16 or BF16 storage a slot first runs in that
 // storage (half the bytes of FP32). Reduced-precision rounding puts a floor
