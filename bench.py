@@ -49,6 +49,8 @@ KERNEL_TRAFFIC_BYTES = {
     ("stream_collide_d3q19_f32_two", 256): 2566221568,
     # k_step_pair<19, StoreF16, shift-fx>, 384^3: mean of two launches (read 2.378 GB + write 2.112 GB)
     ("stream_collide_d3q19_f16_two", 384): 4490235000,
+    # k_step_pair<19, StoreBF16, shift-fx>, 384^3: mean of two launches (read 2.378 GB + write 2.108 GB)
+    ("stream_collide_d3q19_bf16_two", 384): 4486917376,
 }
 
 WORKLOADS = {
