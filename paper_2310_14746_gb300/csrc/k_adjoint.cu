@@ -59,33 +59,60 @@ k_adjoint_step(const typename S::T* __restrict__ fn, const float* __restrict__ l
     const C vp = C(__ldg(varpi + cell));
     const C vx = vp * ux, vy = vp * uy, vz = vp * uz;
     const C vv = vx * vx + vy * vy + vz * vz;
-    const C omega = ph.omega;
 
-    // accumulate b_u = sum lam_i d(M_i/tau + S_i)/du, b_rho = sum lam_i w_i P_i / tau,
-    // and dvarpi = sum lam_i w_i rho (dP/dv . u) / tau
+    // Every sum over directions below is linear in lw_i = lam_i w_i with a
+    // polynomial of degree <= 2 in c_i, so it is a contraction of the moments
+    //   S0 = sum lw_i,  S1 = sum lw_i c_i,  S2 = sum lw_i c_i c_i^T
+    // with v = varpi u, F and u (P_i = 1 + 3 c.v + 4.5 (c.v)^2 - 1.5 v.v,
+    // dP_i/dv = 3 c + 9 (c.v) c - 3 v):
+    //   b_u    = sum lam_i d(M_i/tau + S_i)/du
+    //          = rho varpi omega (3 S1 + 9 S2 v - 3 v S0) + guo (9 S2 F - 3 F S0)
+    //   b_rho  = sum lam_i w_i P_i / tau = omega (S0 + 3 S1.v + 4.5 v.S2 v - 1.5 v.v S0)
+    //   dvarpi = sum lam_i w_i rho (dP_i/dv . u) / tau = rho omega (3 S1.u + 9 v.S2 u - 3 v.u S0)
+    // The moments take only adds of +-lw (c_i has components in {-1, 0, 1},
+    // known at compile time per direction), so the per-cell cost stays close
+    // to the loads and stores.
     C lam[Q];
-    C bux = 0, buy = 0, buz = 0, brho = 0, dvp = 0;
+    C S0 = 0, S1x = 0, S1y = 0, S1z = 0, Sxx = 0, Syy = 0, Szz = 0, Sxy = 0, Sxz = 0, Syz = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         lam[i] = __ldg(lam_in + (I)i * N + cell);
-        const C cx = C(L::cx(i)), cy = C(L::cy(i)), cz = C(L::cz(i));
-        const C w = C(L::w(i));
-        const C cv = cx * vx + cy * vy + cz * vz;
-        const C cF = cx * ph.Fx + cy * ph.Fy + cz * ph.Fz;
-        const C P = C(1) + C(3) * cv + C(4.5) * cv * cv - C(1.5) * vv;
-        // dP/dv = 3 c + 9 (c.v) c - 3 v
-        const C dPx = C(3) * cx + C(9) * cv * cx - C(3) * vx;
-        const C dPy = C(3) * cy + C(9) * cv * cy - C(3) * vy;
-        const C dPz = C(3) * cz + C(9) * cv * cz - C(3) * vz;
-        const C lw = lam[i] * w;
-        const C a = lw * rho * vp * omega;      // d(M_i/tau)/du = w rho varpi dP/dv / tau
-        const C b = lw * ph.guo;                // dS_i/du = guo w (-3 F + 9 (c.F) c)
-        bux += a * dPx + b * (C(-3) * ph.Fx + C(9) * cF * cx);
-        buy += a * dPy + b * (C(-3) * ph.Fy + C(9) * cF * cy);
-        buz += a * dPz + b * (C(-3) * ph.Fz + C(9) * cF * cz);
-        brho += lw * P * omega;
-        dvp += lw * rho * omega * (dPx * ux + dPy * uy + dPz * uz);
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        const C lw = lam[i] * C(L::w(i));
+        S0 += lw;
+        if (cx) {
+            S1x += cx > 0 ? lw : -lw;
+            Sxx += lw;
+        }
+        if (cy) {
+            S1y += cy > 0 ? lw : -lw;
+            Syy += lw;
+        }
+        if (cz) {
+            S1z += cz > 0 ? lw : -lw;
+            Szz += lw;
+        }
+        if (cx && cy) Sxy += cx * cy > 0 ? lw : -lw;
+        if (cx && cz) Sxz += cx * cz > 0 ? lw : -lw;
+        if (cy && cz) Syz += cy * cz > 0 ? lw : -lw;
     }
+    const C omega = ph.omega;
+    // S2 v, S2 F, S2 u
+    const C S2vx = Sxx * vx + Sxy * vy + Sxz * vz, S2vy = Sxy * vx + Syy * vy + Syz * vz,
+            S2vz = Sxz * vx + Syz * vy + Szz * vz;
+    const C S2Fx = Sxx * ph.Fx + Sxy * ph.Fy + Sxz * ph.Fz, S2Fy = Sxy * ph.Fx + Syy * ph.Fy + Syz * ph.Fz,
+            S2Fz = Sxz * ph.Fx + Syz * ph.Fy + Szz * ph.Fz;
+    const C ra = rho * vp * omega;
+    const C bux = ra * (C(3) * S1x + C(9) * S2vx - C(3) * vx * S0) + ph.guo * (C(9) * S2Fx - C(3) * ph.Fx * S0);
+    const C buy = ra * (C(3) * S1y + C(9) * S2vy - C(3) * vy * S0) + ph.guo * (C(9) * S2Fy - C(3) * ph.Fy * S0);
+    const C buz = ra * (C(3) * S1z + C(9) * S2vz - C(3) * vz * S0) + ph.guo * (C(9) * S2Fz - C(3) * ph.Fz * S0);
+    const C S1v = S1x * vx + S1y * vy + S1z * vz;
+    const C vS2v = vx * S2vx + vy * S2vy + vz * S2vz;
+    const C brho = omega * (S0 + C(3) * S1v + C(4.5) * vS2v - C(1.5) * vv * S0);
+    const C S1u = S1x * ux + S1y * uy + S1z * uz;
+    const C vS2u = ux * S2vx + uy * S2vy + uz * S2vz;  // S2 is symmetric: u.S2 v = v.S2 u
+    const C vu = vx * ux + vy * uy + vz * uz;
+    const C dvp = rho * omega * (C(3) * S1u + C(9) * vS2u - C(3) * vu * S0);
     // u = (j + F/2)/rho: du/dj = I/rho, du/drho = -u/rho
     const C a_rho = brho - (bux * ux + buy * uy + buz * uz) * inv_rho;
     const C ajx = bux * inv_rho, ajy = buy * inv_rho, ajz = buz * inv_rho;
@@ -94,7 +121,10 @@ k_adjoint_step(const typename S::T* __restrict__ fn, const float* __restrict__ l
     const C keep = C(1) - omega;
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-        const C mu = keep * lam[k] + a_rho + C(L::cx(k)) * ajx + C(L::cy(k)) * ajy + C(L::cz(k)) * ajz;
+        C mu = fma_(keep, lam[k], a_rho);
+        if (L::cx(k)) mu += L::cx(k) > 0 ? ajx : -ajx;
+        if (L::cy(k)) mu += L::cy(k) > 0 ? ajy : -ajy;
+        if (L::cz(k)) mu += L::cz(k) > 0 ? ajz : -ajz;
         // (S^T mu)_k(y) = mu_k(y + c_k): mu_k(x) goes to y = x - c_k, or, when x - c_k
         // lies beyond a wall, to slot opp(k) of x itself.
         const bool wall = WALLS && nb.template beyond_wall<Q>(k, -1);
