@@ -48,132 +48,16 @@ __device__ __forceinline__ T* scatter_ptr(const Planes<T, Q>& pl, const Nbr<I>& 
 // compiled separately so each kernel carries only its own code and registers.
 enum StepForm { FORM_AUTO = 0, FORM_SHIFT_FX = 1, FORM_SHIFT = 2, FORM_DRAG = 3, FORM_ANISO = 4 };
 
-// Collision of the pull-gathered populations of one cell in the form FORM.
-template <int Q, class S, int FORM>
-__device__ __forceinline__ void collide_form(typename S::C* d, const float* __restrict__ varpi, const Geometry& g,
-                                             const Phys<typename S::C>& ph, typename S::C s, typename S::C inv_s,
-                                             int fx_only, int drag, const float* __restrict__ varpi3, size_t cell) {
-    using C = typename S::C;
-    const bool aniso = FORM == FORM_ANISO || (FORM == FORM_AUTO && varpi3);
-    if (aniso) {  // diagonal porosity tensor [3][cells]
-        collide_aniso<Q, C, S::scaled>(d, C(__ldg(varpi3 + cell)), C(__ldg(varpi3 + g.N + cell)),
-                                       C(__ldg(varpi3 + 2 * g.N + cell)), ph, s, inv_s);
-    } else {
-        const C vp = C(__ldg(varpi + cell));
-        if (FORM == FORM_DRAG || (FORM == FORM_AUTO && drag)) collide_drag<Q, C, S::scaled>(d, vp, ph, s, inv_s);
-        else if (FORM == FORM_SHIFT_FX || (FORM == FORM_AUTO && fx_only))
-            collide<Q, C, S::scaled, true>(d, vp, ph, s, inv_s);
-        else collide<Q, C, S::scaled, false>(d, vp, ph, s, inv_s);
-    }
-}
-
-template <int Q>
-__host__ __device__ constexpr int x_shifted_rank(int i);
-
-// AA odd step of one periodic cell, first half: gather (SWAPPED layout), collide,
-// store the c_x = 0 populations and the x-shifted ones bound outside the
-// block's row segment directly, stage the others for the thread of their
-// target position (stage[rank][thread], raw storage values).
-template <int Q, class S, class I, int FORM>
-__device__ __forceinline__ void aa_odd_collide(const Planes<const typename S::T, Q>& fin,
-                                               const Planes<typename S::T, Q>& fout, const float* __restrict__ varpi,
-                                               const Geometry& g, const Phys<typename S::C>& ph, typename S::C s,
-                                               typename S::C inv_s, int fx_only, int drag,
-                                               const float* __restrict__ varpi3, int x, int y, int z,
-                                               typename S::T* stage) {
-    using C = typename S::C;
-    using L = Lat<Q>;
-    const I cell = (I)x + (I)g.nx * ((I)y + (I)g.ny * (I)z);
-    const Nbr<I> nb(g, x, y, z, 0);
-    C d[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = S::load_raw(gather_ptr<Q, false, SWAPPED>(fin, nb, cell, i), 0);
-    collide_form<Q, S, FORM>(d, varpi, g, ph, s, inv_s, fx_only, drag, varpi3, (size_t)cell);
-    const int bx = blockDim.x, x0 = blockIdx.x * bx;
-    const int t = threadIdx.x + bx * threadIdx.y;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int cx = L::cx(i);
-        const int xt = x + cx;  // unwrapped target column
-        if (cx != 0 && xt >= x0 && xt < x0 + bx && xt >= 0 && xt < g.nx)
-            S::store_raw(stage + x_shifted_rank<Q>(i) * 256 + (t + cx), 0, d[i]);
-        else
-            S::store_raw(scatter_ptr<Q, false, STREAMED>(fout, nb, cell, i), 0, d[i]);
-    }
-}
-
-// Second half, after the block's barrier: the thread of position (x, y, z)
-// stores, for each x-shifted direction, the value staged for it by the cell
-// x - c_x of its row (when that cell is in the block's row segment).
-template <int Q, class S, class I>
-__device__ __forceinline__ void aa_odd_aligned_stores(const Planes<typename S::T, Q>& fout, const Geometry& g, int x,
-                                                      int y, int z, const typename S::T* stage) {
-    using L = Lat<Q>;
-    const I cell = (I)x + (I)g.nx * ((I)y + (I)g.ny * (I)z);
-    const Nbr<I> nb(g, x, y, z, 0);
-    const int bx = blockDim.x, x0 = blockIdx.x * bx, tx = threadIdx.x;
-    const int t = tx + bx * threadIdx.y;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int cx = L::cx(i);
-        if (cx == 0) continue;
-        const int src = tx - cx;
-        if (src < 0 || src >= bx || x0 + src >= g.nx) continue;
-        I o = 0;  // y/z part of the target offset (the row of x + c_i)
-        if (L::cy(i) > 0) o += nb.oyp;
-        if (L::cy(i) < 0) o += nb.oym;
-        if (L::cz(i) > 0) o += nb.ozp;
-        if (L::cz(i) < 0) o += nb.ozm;
-        fout.p[i][cell + o] = stage[x_shifted_rank<Q>(i) * 256 + t];
-    }
-}
-
-// Directions with c_x != 0 and their rank among them (the staged stores below).
-template <int Q>
-__host__ __device__ constexpr int x_shifted_count() {
-    int n = 0;
-    for (int i = 0; i < Q; ++i) n += Lat<Q>::cx(i) != 0;
-    return n;
-}
-template <int Q>
-__host__ __device__ constexpr int x_shifted_rank(int i) {
-    int n = 0;
-    for (int j = 0; j < i; ++j) n += Lat<Q>::cx(j) != 0;
-    return n;
-}
-
-// The odd step of the in-place AA pattern stores every population with c_x != 0
-// to the x-neighbour, so a warp's store of one plane straddles two cache lines
-// (measured: even step 1.00, odd step 0.82 of the copy bandwidth). On periodic
-// lattices the odd step therefore stages those values in shared memory by the
-// row position they are bound for and stores them aligned after a barrier;
-// only values bound across the block's row segment (its two ends, and the
-// periodic wrap) are stored directly. Each stored location belongs to the
-// read set of exactly one cell of the block (the AA pattern reads and writes
-// the same slots per cell), and all of the block's reads precede the barrier,
-// so the in-place update stays race-free.
 template <int Q, class S, bool WALLS, int MODE, class I, int FORM>
 __global__ void __launch_bounds__(256)
 k_step(Planes<const typename S::T, Q> fin, Planes<typename S::T, Q> fout, const float* __restrict__ varpi,
        Geometry g, Phys<typename S::C> ph, typename S::C s, typename S::C inv_s, int fx_only, int drag,
        const float* __restrict__ varpi3, const unsigned* __restrict__ links) {
     using C = typename S::C;
-    using T = typename S::T;
-    constexpr bool STAGE = MODE == MODE_AA_ODD && !WALLS;
-    constexpr int NSH = STAGE ? x_shifted_count<Q>() : 1;
-    __shared__ T stage[NSH][STAGE ? 256 : 1];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    const bool valid = x < g.nx && y < g.ny;
-    if (STAGE) {
-        if (valid) aa_odd_collide<Q, S, I, FORM>(fin, fout, varpi, g, ph, s, inv_s, fx_only, drag, varpi3, x, y, z,
-                                                 &stage[0][0]);
-        __syncthreads();
-        if (valid) aa_odd_aligned_stores<Q, S, I>(fout, g, x, y, z, &stage[0][0]);
-        return;
-    }
-    if (!valid) return;
+    if (x >= g.nx || y >= g.ny) return;
     const I cell = (I)x + (I)g.nx * ((I)y + (I)g.ny * (I)z);
     unsigned lm = 0;
     if (WALLS && links) {

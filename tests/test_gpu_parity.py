@@ -137,10 +137,11 @@ def test_patterns_bitwise_identical_fp32():
 @pytest.mark.parametrize("storage", [hb.HLBM_F32, hb.HLBM_F16DEV])
 @pytest.mark.parametrize("q,shape", [(19, (3, 4, 5)), (19, (4, 5, 45)), (19, (2, 3, 130)), (19, (3, 2, 256)),
                                      (19, (2, 5, 200)), (9, (1, 7, 131)), (9, (1, 3, 64))])
-def test_aa_periodic_staged_stores_bitwise(q, shape, storage):
-    """Fully periodic lattices take the AA odd step with shared-memory staged stores: rows
-    narrower than a warp, one and several 128-cell row segments, ragged last segments. The AA
-    state equals the two-lattice state bit for bit after odd and even step counts."""
+def test_aa_periodic_bitwise(q, shape, storage):
+    """Fully periodic lattices in FP32 and FP16 storage (the in-place kernels without wall
+    logic): rows narrower than a warp, one and several 128-cell row segments, ragged last
+    segments. The AA state equals the two-lattice state bit for bit after odd and even step
+    counts."""
     vp = inputs.random_porosity(shape, seed=18, lo=0.2)
     f0 = inputs.random_populations(q, shape, seed=19, amplitude=0.2)
     F = (1e-5, 2e-6, -3e-6 if q == 19 else 0.0)
