@@ -108,7 +108,8 @@ typedef struct {
  * pattern `pattern`; work goes on `cuda_stream` (a cudaStream_t; NULL is the
  * legacy default stream) of the current device. Defaults: tau = 1, F = 0,
  * all axes periodic, varpi = 1 everywhere, populations at rest (f = w).
- * On error *out is NULL. Cites: the lattice and its data are the problem
+ * Limits: ny and nz at most 65535 (launch-grid dimensions), at most 2^34
+ * cells; HLBM_ERR_INVALID_ARG beyond them. On error *out is NULL. Cites: the lattice and its data are the problem
  * statement of eq. targetEBTL and of the HBGKBE (Sec. 3.2). */
 int hlbm_create(hlbm_t** out, int velset, int nx, int ny, int nz, int storage, int pattern,
                 void* cuda_stream);
@@ -234,6 +235,20 @@ int hlbm_moments_f64(hlbm_t* h, double* rho, double* u, int on_device);
  * replaces. Synchronises. */
 int hlbm_reduce(hlbm_t* h, hlbm_stats* out);
 
+/* Time series of the FP64 diagnostics without a host synchronisation per
+ * sample: records the diagnostics of the current state, then nsamples - 1
+ * times advances `every` time steps and records them again, so record k
+ * describes the state k*every steps after the call began. out receives
+ * nsamples records of 8 doubles in the order mass, momentum[3], plane_flux,
+ * k_app, max_du, max_u (the fields of hlbm_stats); max_du compares with the
+ * residual reference of the last hlbm_reduce call, which this call leaves
+ * unchanged. Used for the relaxation history of the Darcy law with memory
+ * (Sec. 2, the mean momentum of a cell relaxing with no force). A device
+ * `out` (8*nsamples doubles) keeps the call asynchronous; a host `out`
+ * synchronises once at the end (the call then allocates a device staging
+ * buffer for the records). */
+int hlbm_reduce_series(hlbm_t* h, long nsamples, int every, double* out, int on_device);
+
 /* ---- differentiation ---------------------------------------------------- */
 
 /* Gradient of the outflow mass flux through the plane x = plane_x,
@@ -320,7 +335,9 @@ typedef struct {
  * floor, is converted in place to FP32 storage (when the budget allows) and
  * must then meet its tolerance in FP32. Scheduling: every round the oldest
  * live request advances check_every steps, and younger ones join it in age
- * order within a cell budget (hlbm_server_set_priority). */
+ * order within a cell budget (hlbm_server_set_priority). Slots of at least
+ * 2^19 cells run the single-lattice step kernels inside the round's graph;
+ * smaller ones share a batched kernel; both give the same bits. */
 int hlbm_server_create(hlbm_server_t** out, size_t mem_budget, int storage, int check_every,
                        void* cuda_stream);
 /* Turn refinement on or off and set its floor coefficient (>= 0). With it off,
@@ -329,10 +346,10 @@ int hlbm_server_create(hlbm_server_t** out, size_t mem_budget, int storage, int 
 int hlbm_server_set_refinement(hlbm_server_t* s, int enable, double floor_coef);
 /* Age priority of the batch (no counterpart in the paper: a serving policy).
  * Each round runs the oldest live request and, in age order, the younger
- * ones that fit a budget of max(4M, (1 + backfill) * the oldest request's
+ * ones that fit a budget of max(1M, (1 + backfill) * the oldest request's
  * cells) cells; a younger request that does not fit is skipped for that
  * round, so smaller ones behind it can still run. backfill >= 0 (default
- * 0.25) bounds how much the oldest request is slowed by the batch, whatever
+ * 0.1) bounds how much the oldest request is slowed by the batch, whatever
  * the queue length; a very large value is plain processor sharing. Results
  * do not depend on it, only when they arrive. */
 int hlbm_server_set_priority(hlbm_server_t* s, double backfill);
@@ -368,21 +385,29 @@ void hlbm_server_destroy(hlbm_server_t* s);
  * buffer of 3*nx*ny*nz values in the arithmetic type (double for HLBM_F64,
  * float otherwise) holding the previous velocity, which the call compares
  * against (max_du) and then overwrites with the current velocity; the lattice
- * description (velset, sizes, storage, bc[3] boundary types, tau, F[3]); and
- * the host struct `out` (its step field is set to 0). The call uses no
- * memory the library allocates: its scratch is a fixed 4 MiB array in the
- * library's device memory, which every GPU that loads the library keeps
- * until the process exits. A lattice whose reduction needs more than 65536
- * partial blocks (blocks of 256 threads over x-rows of up to 128 cells and
- * four z planes; 384^3 is the largest cube that fits) returns
- * HLBM_ERR_SCRATCH_LIMIT. The first
- * call on a device looks up the array's device address (once per device);
- * make that first call before any stream capture. Every call on a device
- * shares the array: calls whose work overlaps on the same GPU race on it, so
- * serialise them. Synchronises `cuda_stream`. */
+ * description (velset, sizes, storage, bc[3] boundary types, tau, F[3],
+ * storage_scale with the rule of hlbm_set_storage_scale); the homogenization
+ * `form` (HLBM_HOMOG_SHIFT or HLBM_HOMOG_DRAG, as hlbm_set_homogenization)
+ * with `varpi`, nx*ny*nz device FP32 porosity values that the drag form needs
+ * for its velocity (required with HLBM_HOMOG_DRAG, ignored and may be NULL
+ * with HLBM_HOMOG_SHIFT); and the host struct `out` (its step field is set to
+ * 0). Lattices with resolved obstacles (hlbm_set_solid_mask) are not
+ * supported: the call has no solid-cell input and counts every cell as fluid.
+ * Sizes follow hlbm_create's limits, and the reduction grid must fit the
+ * launch limits; otherwise HLBM_ERR_INVALID_ARG.
+ * The call uses no memory the library allocates: its scratch is a fixed 4 MiB
+ * array in the library's device memory, which every GPU that loads the
+ * library keeps until the process exits. A lattice whose reduction needs more
+ * than 65536 partial blocks (blocks of 256 threads over x-rows of up to 128
+ * cells and four z planes; 384^3 is the largest cube that fits) returns
+ * HLBM_ERR_SCRATCH_LIMIT. The first call on a device looks up the array's
+ * device address (once per device); make that first call before any stream
+ * capture. Every call on a device shares the array: calls whose work
+ * overlaps on the same GPU race on it, so serialise them. Synchronises
+ * `cuda_stream`. */
 int hlbm_reduce_noalloc(int velset, int nx, int ny, int nz, int storage, const int* bc, double tau,
-                        const double* F, double storage_scale, const void* f, void* u_prev,
-                        hlbm_stats* out, void* cuda_stream);
+                        const double* F, double storage_scale, int form, const float* varpi, const void* f,
+                        void* u_prev, hlbm_stats* out, void* cuda_stream);
 
 /* ---- misc -------------------------------------------------------------- */
 

@@ -52,6 +52,7 @@ HLBM_HOMOG_DRAG = 1
 HLBM_STEP_AUTO = 0
 HLBM_STEP_PER_CELL = 1
 
+STAT_KEYS = ("mass", "mom_x", "mom_y", "mom_z", "plane_flux", "k_app", "max_du", "max_u")
 STORAGE_BYTES = {HLBM_F64: 8, HLBM_F32: 4, HLBM_F16DEV: 2, HLBM_BF16DEV: 2}
 STORAGE_NAMES = {HLBM_F64: "f64", HLBM_F32: "f32", HLBM_F16DEV: "f16dev", HLBM_BF16DEV: "bf16dev"}
 
@@ -147,8 +148,9 @@ SIGNATURES = {
     "hlbm_server_info": (_i, [_vp, ctypes.POINTER(hlbm_server_stats)]),
     "hlbm_server_inject_alloc_failures": (_i, [_vp, _i]),
     "hlbm_server_destroy": (None, [_vp]),
-    "hlbm_reduce_noalloc": (_i, [_i, _i, _i, _i, _i, ctypes.POINTER(_i), _d, ctypes.POINTER(_d), _d, _vp, _vp,
-                                 ctypes.POINTER(hlbm_stats), _vp]),
+    "hlbm_reduce_series": (_i, [_vp, ctypes.c_long, _i, _vp, _i]),
+    "hlbm_reduce_noalloc": (_i, [_i, _i, _i, _i, _i, ctypes.POINTER(_i), _d, ctypes.POINTER(_d), _d, _i, _vp,
+                                 _vp, _vp, ctypes.POINTER(hlbm_stats), _vp]),
     "hlbm_strerror": (ctypes.c_char_p, [_i]),
     "hlbm_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -344,6 +346,13 @@ def hlbm_reduce(h):
     return st.as_dict()
 
 
+def hlbm_reduce_series(h, nsamples, every, out):
+    """Writes nsamples records of the 8 FP64 diagnostics into out (float64 numpy array or CUDA
+    tensor of 8*nsamples values); record k is the state k*every steps after the call began."""
+    p, dev = _ptr(out, np.float64)
+    _check(_lib().hlbm_reduce_series(h, int(nsamples), int(every), p, dev), "hlbm_reduce_series")
+
+
 def hlbm_adjoint_flux_grad(h, nsteps, ckpt_every, plane_x, grad):
     """Returns J; writes dJ/dvarpi into grad (float32 numpy array or CUDA tensor)."""
     p, dev = _ptr(grad, np.float32)
@@ -414,17 +423,18 @@ def hlbm_server_destroy(s):
     _lib().hlbm_server_destroy(s)
 
 
-def hlbm_reduce_noalloc(velset, nx, ny, nz, storage, bc, tau, F, storage_scale, f, u_prev, stream=None):
-    """Diagnostics without any device allocation; f and u_prev are device buffers
-    (CUDA tensors or raw pointers) the caller owns. Returns the stats dict."""
-    fp = f if isinstance(f, int) else f.data_ptr()
-    up = u_prev if isinstance(u_prev, int) else u_prev.data_ptr()
+def hlbm_reduce_noalloc(velset, nx, ny, nz, storage, bc, tau, F, storage_scale, f, u_prev, stream=None,
+                        form=0, varpi=None):
+    """Diagnostics without any device allocation; f, u_prev and (for the drag form) varpi are
+    device buffers (CUDA tensors or raw pointers) the caller owns. Returns the stats dict."""
+    def ptr(t):
+        return None if t is None else (t if isinstance(t, int) else t.data_ptr())
     st = hlbm_stats()
     b = (_i * 3)(*bc)
     FF = (_d * 3)(*F)
     s = current_stream() if stream is None else stream
-    _check(_lib().hlbm_reduce_noalloc(velset, nx, ny, nz, storage, b, float(tau), FF, float(storage_scale), fp, up,
-                                      ctypes.byref(st), s), "hlbm_reduce_noalloc")
+    _check(_lib().hlbm_reduce_noalloc(velset, nx, ny, nz, storage, b, float(tau), FF, float(storage_scale), int(form),
+                                      ptr(varpi), ptr(f), ptr(u_prev), ctypes.byref(st), s), "hlbm_reduce_noalloc")
     return st.as_dict()
 
 
@@ -525,6 +535,14 @@ class Lattice:
 
     def reduce(self):
         return hlbm_reduce(self.h)
+
+    def reduce_series(self, nsamples, every=1, out=None):
+        """(nsamples, 8) FP64 diagnostics records, one every `every` steps from the current state
+        (columns in the order of STAT_KEYS); out may be a CUDA tensor (asynchronous)."""
+        if out is None:
+            out = np.empty((nsamples, 8), dtype=np.float64)
+        hlbm_reduce_series(self.h, nsamples, every, out)
+        return out
 
     def adjoint_flux_grad(self, nsteps, ckpt_every=45, plane_x=None, grad=None):
         """(J, dJ/dvarpi) of the outflow flux through x = plane_x (default nx-1) after nsteps."""

@@ -251,7 +251,7 @@ int hlbm_create(hlbm_t** out, int velset, int nx, int ny, int nz, int storage, i
     if (velset == HLBM_D2Q9 && nz != 1) return HLBM_ERR_INVALID_ARG;
     if (storage < HLBM_F64 || storage > HLBM_BF16DEV) return HLBM_ERR_INVALID_ARG;
     if (pattern != HLBM_TWO_LATTICE && pattern != HLBM_AA) return HLBM_ERR_INVALID_ARG;
-    if (ny > 65535 * 8 || nz > 65535) return HLBM_ERR_INVALID_ARG;
+    if (ny > 65535 || nz > 65535) return HLBM_ERR_INVALID_ARG;  // launch-grid y and z limits
     const size_t cells = (size_t)nx * ny * nz;
     if (cells > ((size_t)1 << 34)) return HLBM_ERR_INVALID_ARG;
 
@@ -602,6 +602,32 @@ int hlbm_reduce(hlbm_t* h, hlbm_stats* out) {
     out->max_u = v[7];
     out->step = h->step;
     return HLBM_OK;
+}
+
+int hlbm_reduce_series(hlbm_t* h, long nsamples, int every, double* out, int on_device) {
+    if (!h || !out || nsamples < 1 || every < 1) return HLBM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    const size_t bytes = (size_t)nsamples * 8 * sizeof(double);
+    double* dst = out;
+    if (!on_device) HLBM_CUDA(cudaMallocAsync((void**)&dst, bytes, h->stream));
+    int rc = HLBM_OK;
+    for (long k = 0; k < nsamples && rc == HLBM_OK; ++k) {
+        if (k) rc = hlbm_step(h, every);
+        if (rc == HLBM_OK) {
+            const cudaError_t e = launch_reduce(h->ctx(h->stream), h->layout(), h->state(), h->u_prev, 0,
+                                                h->partials, dst + 8 * k);
+            if (e != cudaSuccess) rc = cuda_fail(e);
+        }
+    }
+    if (!on_device) {
+        cudaError_t e = cudaSuccess;
+        if (rc == HLBM_OK) e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, h->stream);
+        const cudaError_t ef = cudaFreeAsync(dst, h->stream);
+        if (e == cudaSuccess) e = ef;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (rc == HLBM_OK && e != cudaSuccess) rc = cuda_fail(e);
+    }
+    return rc;
 }
 
 namespace {

@@ -49,6 +49,8 @@ cudaError_t launch_moments(const LaunchCtx& c, int layout, const void* f, void* 
 // if update_prev, overwritten. `partials` is caller-provided scratch of at
 // least reduce_partials_count(c) * 8 doubles.
 size_t reduce_partials_count(const LaunchCtx& c);
+// Whether the partials kernel's grid for this lattice is within the launch limits.
+bool reduce_grid_fits(const LaunchCtx& c);
 cudaError_t launch_reduce(const LaunchCtx& c, int layout, const void* f, void* u_prev,
                           int update_prev, double* partials, double* out8);
 

@@ -184,6 +184,12 @@ size_t reduce_partials_count(const LaunchCtx& c) {
     return (size_t)((c.nx + blk.x - 1) / blk.x) * ((c.ny + blk.y - 1) / blk.y) * ((c.nz + kReduceZ - 1) / kReduceZ);
 }
 
+bool reduce_grid_fits(const LaunchCtx& c) {
+    const dim3 blk = block_for(c.nx);
+    return (size_t)(c.ny + blk.y - 1) / blk.y <= 65535 && (size_t)(c.nz + kReduceZ - 1) / kReduceZ <= 65535 &&
+           (size_t)(c.nx + blk.x - 1) / blk.x <= 0x7fffffff;
+}
+
 template <int Q, class S, bool WALLS>
 static cudaError_t reduce_impl(const LaunchCtx& c, int lay, const void* f, void* u_prev, int upd,
                                double* partials, double* out8) {

@@ -56,17 +56,29 @@ cudaError_t scratch_for_current_device(double** out) {
     return cudaSuccess;
 }
 
+// The storage-scale rule of hlbm_set_storage_scale: a power of two in [1, 2^20]
+// for FP16 deviations, exactly 1 for the other storage types.
+bool scale_ok(int storage, double s) {
+    if (!std::isfinite(s)) return false;
+    if (storage != HLBM_F16DEV) return s == 1.0;
+    int ex = 0;
+    return std::frexp(s, &ex) == 0.5 && s >= 1.0 && s <= 1048576.0;
+}
+
 }  // namespace
 
 extern "C" int hlbm_reduce_noalloc(int velset, int nx, int ny, int nz, int storage, const int* bc, double tau,
-                                   const double* F, double storage_scale, const void* f, void* u_prev,
-                                   hlbm_stats* out, void* cuda_stream) {
+                                   const double* F, double storage_scale, int form, const float* varpi,
+                                   const void* f, void* u_prev, hlbm_stats* out, void* cuda_stream) {
     if (!f || !u_prev || !out || !bc || !F) return HLBM_ERR_INVALID_ARG;
     if (velset != HLBM_D2Q9 && velset != HLBM_D3Q19) return HLBM_ERR_INVALID_ARG;
     if (nx < 1 || ny < 1 || nz < 1 || (velset == HLBM_D2Q9 && nz != 1)) return HLBM_ERR_INVALID_ARG;
+    // the size limits of hlbm_create
+    if (ny > 65535 || nz > 65535 || (size_t)nx * ny * nz > ((size_t)1 << 34)) return HLBM_ERR_INVALID_ARG;
     if (storage < HLBM_F64 || storage > HLBM_BF16DEV) return HLBM_ERR_INVALID_ARG;
-    if (!(tau > 0.5) || !std::isfinite(tau) || !(storage_scale > 0.0) || !std::isfinite(storage_scale))
-        return HLBM_ERR_INVALID_ARG;
+    if (!(tau > 0.5) || !std::isfinite(tau) || !scale_ok(storage, storage_scale)) return HLBM_ERR_INVALID_ARG;
+    if (form != HLBM_HOMOG_SHIFT && form != HLBM_HOMOG_DRAG) return HLBM_ERR_INVALID_ARG;
+    if (form == HLBM_HOMOG_DRAG && !varpi) return HLBM_ERR_INVALID_ARG;
     hlbm::LaunchCtx c;
     c.q = velset;
     c.storage = storage;
@@ -82,6 +94,9 @@ extern "C" int hlbm_reduce_noalloc(int velset, int nx, int ny, int nz, int stora
     c.tau = tau;
     c.scale = storage_scale;
     c.stream = static_cast<cudaStream_t>(cuda_stream);
+    c.drag = form == HLBM_HOMOG_DRAG;
+    c.varpi = c.drag ? varpi : nullptr;  // the shift form's moments do not depend on varpi
+    if (!hlbm::reduce_grid_fits(c)) return HLBM_ERR_INVALID_ARG;
     if (hlbm::reduce_partials_count(c) > kMaxPartialBlocks) return HLBM_ERR_SCRATCH_LIMIT;
 
     double* scratch = nullptr;

@@ -26,8 +26,10 @@ from . import HLBM_D3Q19, HLBM_F32, HLBM_TWO_LATTICE, Lattice
 
 
 def memory_kernel(varpi, tau, steps, u0=1e-4, axis=0, storage=HLBM_F32, pattern=HLBM_TWO_LATTICE,
-                  velset=HLBM_D3Q19, stop_below=0.0):
-    """Return A~_n for n = 0..steps-1 (numpy float64), stopping early once |A~_n| < stop_below."""
+                  velset=HLBM_D3Q19, stop_below=0.0, chunk=4096):
+    """Return A~_n for n = 0..steps-1 (numpy float64), stopping early once |A~_n| < stop_below.
+    The mean momentum is recorded on the device after every step (hlbm_reduce_series) and read
+    back once per chunk of steps, so the host never waits on a single step."""
     varpi = np.ascontiguousarray(varpi, dtype=np.float32)
     nz, ny, nx = varpi.shape
     cells = nx * ny * nz
@@ -39,15 +41,22 @@ def memory_kernel(varpi, tau, steps, u0=1e-4, axis=0, storage=HLBM_F32, pattern=
         u = [0.0, 0.0, 0.0]
         u[axis] = u0
         lat.init_equilibrium(1.0, u)
-        key = ("mom_x", "mom_y", "mom_z")[axis]
+        col = 1 + axis  # mom_x, mom_y, mom_z
         out = []
-        for _ in range(steps):
-            a = lat.reduce()[key] / cells / u0
+        done = 0
+        while done < steps:
+            m = min(chunk, steps - done)
+            if done:
+                lat.step(1)  # the first record of a chunk is the state one step after the last one
+            a = lat.reduce_series(m, 1)[:, col] / cells / u0
+            if stop_below:
+                small = np.nonzero(np.abs(a) < stop_below)[0]
+                if small.size:
+                    out.append(a[:small[0] + 1])
+                    break
             out.append(a)
-            if stop_below and abs(a) < stop_below:
-                break
-            lat.step(1)
-        return np.array(out)
+            done += m
+        return np.concatenate(out)
     finally:
         lat.close()
 

@@ -57,3 +57,38 @@ def test_sphere_cell_matches_oracle_and_steady_permeability(oracle):
     lat.close()
     assert abs(a[-1]) < 1e-6 * a[0]
     assert abs(a.sum() - st["k_app"] / nu) / (st["k_app"] / nu) < 2e-3
+
+
+def test_reduce_series_equals_reduce_loop():
+    """The device-side diagnostics series gives the same records as one hlbm_reduce per sample
+    (same kernels), apart from the residual, which the series takes against the unchanged
+    reference of the last hlbm_reduce call."""
+    import torch
+    shape = (6, 7, 40)
+    vp = inputs.random_porosity(shape, seed=51, lo=0.3)
+    f0 = inputs.random_populations(19, shape, seed=52, amplitude=0.05)
+    F = (1e-5, 2e-6, 0.0)
+    a = make_lattice(19, shape, hb.HLBM_F32, hb.HLBM_AA, 0.7, F, (0, 1, 0), varpi=vp, f0=f0)
+    b = make_lattice(19, shape, hb.HLBM_F32, hb.HLBM_AA, 0.7, F, (0, 1, 0), varpi=vp, f0=f0)
+    a.reduce()
+    b.reduce()
+    rec = a.reduce_series(6, 3)
+    dev = torch.empty((6, 8), dtype=torch.float64, device="cuda")
+    a.reduce_series(6, 3, out=dev)  # device records, asynchronous
+    torch.cuda.synchronize()
+    loop = []
+    for k in range(6):
+        if k:
+            b.step(3)
+        st = b.reduce()
+        loop.append([st[key] for key in hb.STAT_KEYS])
+    loop = np.array(loop)
+    cols = [0, 1, 2, 3, 4, 5, 7]  # all but max_du
+    np.testing.assert_array_equal(rec[:, cols], loop[:, cols])
+    a2 = make_lattice(19, shape, hb.HLBM_F32, hb.HLBM_AA, 0.7, F, (0, 1, 0), varpi=vp, f0=f0)
+    a2.step(30)  # the second series began where the first one ended (15 steps in)
+    st = a2.reduce()
+    np.testing.assert_array_equal(dev.cpu().numpy()[5, cols], [st[key] for key in hb.STAT_KEYS if key != "max_du"])
+    assert a.steps_taken == 30
+    for lat in (a, b, a2):
+        lat.close()
