@@ -46,6 +46,18 @@ namespace hlbm {
 namespace srv {
 
 constexpr int kMaxSlots = 1024;
+// Kernel classes: 2 * storage + fast for the tile kernel (2..7), and kDirectClass
+// for the large slots that run the single-lattice kernels.
+constexpr int kDirectClass = 8;
+constexpr int kClasses = 9;
+// Slots of at least this many cells (96^3 and larger at the serving edges) run the
+// single-lattice step kernels, one launch per slot and step inside the round's
+// graph: such a slot fills the GPU on its own, and the tile kernel's per-block
+// slot lookup (a chain of dependent loads before the first population load)
+// costs it 10 to 15 % of the copy bandwidth (measured: 128^3 FP32 0.90 vs 0.99,
+// 192^3 FP16 0.70 vs 0.83). Smaller slots share the tile kernel, where one launch
+// per class replaces one per slot.
+constexpr size_t kDirectCells = (size_t)1 << 19;
 constexpr int kBlock = 256;  // threads per block; a tile is tw x (256 / tw) threads of one slot
 
 struct DevSlot {
@@ -61,6 +73,7 @@ struct DevSlot {
     int ntiles;
     int storage;  // HLBM_F32, HLBM_F16DEV or HLBM_BF16DEV
     int fx_only;  // body force along x only
+    int direct;   // advanced by the single-lattice step kernels (a large slot), not the tile kernel
     float scale, inv_scale;
     Phys<float> ph;
     double nu, Fx64;
@@ -69,7 +82,7 @@ struct DevSlot {
 struct DevTable {
     int nslots;
     int total_tiles;
-    int lo[8], hi[8];       // tile range of each kernel class (kernel_class below)
+    int lo[kClasses], hi[kClasses];  // tile range of each kernel class (kernel_class below)
     int begin[kMaxSlots];   // first tile of each slot (ascending): the slot lookup reads only this
     DevSlot slot[kMaxSlots];
 };
@@ -89,6 +102,7 @@ __device__ __forceinline__ int find_slot(const DevTable* tab, int t, int ns) {
 // case, compiled on its own for 64 registers), else 2 * storage. The table
 // keeps the slots of a class contiguous.
 __host__ __device__ inline int kernel_class(const DevSlot& d) {
+    if (d.direct) return kDirectClass;
     const bool fast = d.fx_only && (d.storage == HLBM_F32 || d.pair);
     return 2 * d.storage + (fast ? 1 : 0);
 }
@@ -399,7 +413,7 @@ struct hlbm_server {
     int check_every = 100;
     int refine = 1;             // move reduced-precision slots to FP32 at their floor
     double floor_coef = 2e-3;   // reduced-precision residual floor, in units of max|u|
-    double backfill = 0.25;     // cells younger requests may add to a round, per cell of the oldest
+    double backfill = 0.1;      // cells younger requests may add to a round, per cell of the oldest
     std::vector<int> run;       // live slots (indices) that run this round, in table order
     std::vector<uint64_t> table_ids;  // request ids of the slots in the device table, in order
     size_t budget = 0, used = 0;
@@ -413,7 +427,9 @@ struct hlbm_server {
     DevTable* htab = nullptr;
     bool table_dirty = true;
     cudaGraphExec_t gexec = nullptr;
-    int grid[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // blocks of the captured launches per kernel class (>= its tiles)
+    int grid[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // blocks of the captured launches per tile-kernel class (>= its tiles)
+    // large slots advanced by single-lattice launches in the captured graph: (id, storage) of each
+    std::vector<std::pair<uint64_t, int>> graph_direct;
     double* dpartials = nullptr;
     size_t partial_cap = 0;  // tiles
     double* dout = nullptr;
@@ -535,6 +551,7 @@ cudaError_t admit(hlbm_server_t* s, Pending& p, Live& l) {
     l.ds.ny = r.ny;
     l.ds.nz = r.nz;
     l.ds.fx_only = r.F[1] == 0.0 && r.F[2] == 0.0;
+    l.ds.direct = n >= kDirectCells ? 1 : 0;
     l.ds.storage = s->storage;
     set_tiles(l.ds);
     l.ds.scale = (float)scale_of(s->storage);
@@ -604,22 +621,42 @@ int build_graph(hlbm_server_t* s) {
     if (!s->cap_stream) SRV_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     SRV_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    const auto launch = [&](auto kern, int blocks, int k) {
+        if (blocks > 0 && le == cudaSuccess) {
+            kern<<<blocks, kBlock, 0, s->cap_stream>>>(s->dtab, k);
+            le = cudaGetLastError();
+        }
+    };
+    s->graph_direct.clear();
+    std::vector<const Live*> direct;
+    for (int idx : s->run) {
+        const Live& l = s->live[idx];
+        if (l.ds.direct) {
+            direct.push_back(&l);
+            s->graph_direct.emplace_back(l.p.id, l.ds.storage);
+        }
+    }
     for (int k = 0; k < s->check_every; ++k) {
         const int* g = s->grid;
-        if (g[2 * HLBM_F16DEV + 1] > 0)
-            k_batched_step<StoreF16, true><<<g[2 * HLBM_F16DEV + 1], kBlock, 0, s->cap_stream>>>(s->dtab, k);
-        if (g[2 * HLBM_F16DEV] > 0)
-            k_batched_step<StoreF16, false><<<g[2 * HLBM_F16DEV], kBlock, 0, s->cap_stream>>>(s->dtab, k);
-        if (g[2 * HLBM_BF16DEV + 1] > 0)
-            k_batched_step<StoreBF16, true><<<g[2 * HLBM_BF16DEV + 1], kBlock, 0, s->cap_stream>>>(s->dtab, k);
-        if (g[2 * HLBM_BF16DEV] > 0)
-            k_batched_step<StoreBF16, false><<<g[2 * HLBM_BF16DEV], kBlock, 0, s->cap_stream>>>(s->dtab, k);
-        if (g[2 * HLBM_F32 + 1] > 0)
-            k_batched_step<StoreF32, true><<<g[2 * HLBM_F32 + 1], kBlock, 0, s->cap_stream>>>(s->dtab, k);
-        if (g[2 * HLBM_F32] > 0)
-            k_batched_step<StoreF32, false><<<g[2 * HLBM_F32], kBlock, 0, s->cap_stream>>>(s->dtab, k);
+        for (const Live* l : direct) {  // launch k reads f[k & 1], writes f[(k + 1) & 1]
+            if (le != cudaSuccess) break;
+            LaunchCtx c = s->ctx_for(*l);
+            c.stream = s->cap_stream;
+            le = launch_step(c, MODE_TWO_LATTICE, l->ds.f[k & 1], l->ds.f[(k + 1) & 1], l->ds.varpi);
+        }
+        launch(k_batched_step<StoreF16, true>, g[2 * HLBM_F16DEV + 1], k);
+        launch(k_batched_step<StoreF16, false>, g[2 * HLBM_F16DEV], k);
+        launch(k_batched_step<StoreBF16, true>, g[2 * HLBM_BF16DEV + 1], k);
+        launch(k_batched_step<StoreBF16, false>, g[2 * HLBM_BF16DEV], k);
+        launch(k_batched_step<StoreF32, true>, g[2 * HLBM_F32 + 1], k);
+        launch(k_batched_step<StoreF32, false>, g[2 * HLBM_F32], k);
     }
     cudaError_t e = cudaStreamEndCapture(s->cap_stream, &graph);
+    if (e == cudaSuccess && le != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        e = le;
+    }
     if (e != cudaSuccess) return srv_cuda_fail(e);
     if (s->gexec) {
         cudaGraphExecDestroy(s->gexec);
@@ -649,10 +686,13 @@ int fit_grid(int cur, int tiles) {
 // its speed alone, however long the queue behind it: the batch approaches
 // first-come first-served for long solves (which bounds the tail) while short
 // requests fill the rest of each round. kRoundCells keeps a small oldest
-// request from leaving the GPU idle. A very large backfill is plain processor
+// request from leaving the GPU idle: about a million cells (some 4000 blocks
+// of 256 cells, six waves over 152 SMs) keep every SM streaming, and a larger
+// floor would let younger requests slow an oldest request of 128^3 (2.1M
+// cells) by far more than the backfill allows. A very large backfill is plain processor
 // sharing. Returns true when the set (or its order) differs from the device
 // table.
-constexpr double kRoundCells = 4.0e6;
+constexpr double kRoundCells = 1.0e6;
 
 bool choose_run(hlbm_server_t* s) {
     std::vector<int> age(s->live.size());
@@ -687,7 +727,7 @@ int upload_table(hlbm_server_t* s) {
     int tiles = 0;
     s->htab->nslots = (int)s->run.size();
     s->table_ids.clear();
-    for (int c = 0; c < 8; ++c) s->htab->lo[c] = s->htab->hi[c] = 0;
+    for (int c = 0; c < kClasses; ++c) s->htab->lo[c] = s->htab->hi[c] = 0;
     for (size_t k = 0; k < s->run.size(); ++k) {
         Live& l = s->live[s->run[k]];
         const int c = kernel_class(l.ds);
@@ -712,6 +752,12 @@ int upload_table(hlbm_server_t* s) {
     SRV_CUDA(cudaMemcpyAsync(s->dtab, s->htab, bytes, cudaMemcpyHostToDevice, s->stream));
     s->table_dirty = false;
     bool rebuild = !s->gexec;
+    {  // the large slots are launched one by one: a change in their set needs a new graph
+        std::vector<std::pair<uint64_t, int>> direct;
+        for (int idx : s->run)
+            if (s->live[idx].ds.direct) direct.emplace_back(s->live[idx].p.id, s->live[idx].ds.storage);
+        rebuild = rebuild || direct != s->graph_direct;
+    }
     for (int c = 0; c < 8; ++c) {
         const int gc = fit_grid(s->grid[c], s->htab->hi[c] - s->htab->lo[c]);
         rebuild = rebuild || gc != s->grid[c];
