@@ -42,16 +42,38 @@ METRIC = "D3Q19 HBGK MLUPS & % HBM roofline; p50/p99 solve latency, batched vs p
 FALLBACK_HBM_GBS = 6800.0
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from the
-# ncu capture summarised under profiles/ (None until captured for the current kernel).
+# ncu capture summarised under profiles/. Each entry records the hash of the step-kernel
+# sources it was captured from (kernel_source_hash()); when the sources have changed since,
+# the bench reports traffic as null instead of a stale figure.
 KERNEL_TRAFFIC_BYTES = {
     # k_step<19, StoreF32, periodic, two-lattice, int, shift-fx>, 256^3: mean of two launches
-    # (1342212864 + 1229032448 and 1342241536 + 1218956288 bytes)
-    ("stream_collide_d3q19_f32_two", 256): 2566221568,
-    # k_step_pair<19, StoreF16, shift-fx>, 384^3: mean of two launches (read 2.378 GB + write 2.112 GB)
-    ("stream_collide_d3q19_f16_two", 384): 4490235000,
-    # k_step_pair<19, StoreBF16, shift-fx>, 384^3: mean of two launches (read 2.378 GB + write 2.108 GB)
-    ("stream_collide_d3q19_bf16_two", 384): 4486917376,
+    # (1342211840 + 1221328384 and 1342430208 + 1225819136 bytes)
+    ("stream_collide_d3q19_f32_two", 256): {"bytes": 2565894784, "source_hash": "8cf1f08c6b6347f2"},
 }
+
+STEP_KERNEL_SOURCES = ("lattice.cuh", "k_step.cuh", "k_step_pair.cuh", "k_step.cu", "k_step_f64.cu",
+                       "k_step_f32.cu", "k_step_f16.cu", "k_step_bf16.cu")
+
+
+def kernel_source_hash():
+    """sha256 (first 16 hex digits) over the sources of the step kernels."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in STEP_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2310_14746_gb300", "csrc", name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def kernel_traffic(kname, n):
+    """(bytes per launch or None, note) for the kernel as it is now."""
+    e = KERNEL_TRAFFIC_BYTES.get((kname, n))
+    if e is None:
+        return None, "not captured"
+    if e["source_hash"] != kernel_source_hash():
+        return None, "stale: kernel sources changed since the capture"
+    return e["bytes"], "ncu capture of these sources"
+
 
 WORKLOADS = {
     "d3q19_256_f32": dict(q=19, n=256, storage="f32", pattern="two", tau=0.6, F=(1e-6, 0.0, 0.0),
@@ -70,11 +92,14 @@ WORKLOADS = {
     "d3q19_256_f16": dict(q=19, n=256, storage="f16", pattern="two", tau=0.6, F=(1e-6, 0.0, 0.0),
                           period=32, ratio=0.3, desc="as d3q19_256_f32 with FP16 deviation storage"),
     "d3q19_384_f16": dict(q=19, n=384, storage="f16", pattern="two", tau=0.6, F=(1e-6, 0.0, 0.0),
-                          period=32, ratio=0.3,
-                          desc="D3Q19 HBGK 384^3 periodic sphere matrix, FP16 deviation storage (s = 2^12)"),
+                          field="boolean",
+                          desc="D3Q19 HBGK 384^3 random periodic Boolean sphere matrix (seeded, radius "
+                               "P*U[0.1,0.45], P = 32, phi* ~ U[0.4,0.9]), F = 1e-6, tau = 0.6, FP16 deviation "
+                               "storage (s = 2^12), two-lattice"),
     "d3q19_384_bf16": dict(q=19, n=384, storage="bf16", pattern="two", tau=0.6, F=(1e-6, 0.0, 0.0),
-                           period=32, ratio=0.3,
-                           desc="D3Q19 HBGK 384^3 periodic sphere matrix, BF16 deviation storage"),
+                           field="boolean",
+                           desc="D3Q19 HBGK 384^3 random periodic Boolean sphere matrix (as d3q19_384_f16), "
+                                "BF16 deviation storage, two-lattice"),
 }
 
 
@@ -179,21 +204,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_field(w):
+BOOLEAN_SEED = 2310147460 + 3  # seed of the random sphere-matrix workload
+
+
+def make_field(w, render_n=None):
+    """The porosity-control field of a workload: the regular sphere matrix, or the seeded random
+    Boolean matrix (rendered at render_n to sample the same continuous geometry on a coarser grid)."""
     from paper_2310_14746_gb300 import inputs
-    return inputs.regular_sphere_field(w["n"], period=w["period"], radius_ratio=w["ratio"])
+    if w.get("field") == "boolean":
+        return inputs.random_sphere_field(w["n"], BOOLEAN_SEED, render_n=render_n)[0]
+    return inputs.regular_sphere_field(render_n or w["n"], period=w["period"], radius_ratio=w["ratio"])
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle timing (baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
 
-def oracle_mlups(w, varpi, steps=None, budget_s=15.0):
+def oracle_mlups(w, varpi, steps=None, budget_s=15.0, threads=None):
     """FP64 oracle MLUPS on the full lattice of the workload; times `steps` time steps, or
-    as many as fit in ~budget_s after a 1-step probe. Returns (mlups, steps, seconds, cores)."""
+    as many as fit in ~budget_s after a 1-step probe. threads: OpenMP threads (default: all
+    host cores). Returns (mlups, steps, seconds, threads used)."""
     import oracle
-    cores = os.cpu_count() or 1
-    oracle.set_threads(cores)
+    oracle.set_threads(threads or os.cpu_count() or 1)
     q, n = w["q"], w["n"]
     f = oracle.equilibrium_state(q, (n, n, n))
     vp = varpi.astype(np.float64)
@@ -205,7 +237,27 @@ def oracle_mlups(w, varpi, steps=None, budget_s=15.0):
     t0 = time.perf_counter()
     f = oracle.run(f, vp, w["tau"], w["F"], (0, 0, 0), steps)
     dt = time.perf_counter() - t0
-    return n ** 3 * steps / dt / 1e6, steps, dt, oracle.get_threads()
+    used = oracle.get_threads()
+    oracle.set_threads(os.cpu_count() or 1)
+    return n ** 3 * steps / dt / 1e6, steps, dt, used
+
+
+def oracle_reference_96(w, field96, steps):
+    """CPU-baseline run of the FP64 oracle at the error-check size of the random-sphere workload
+    (96^3, the same continuous geometry, `steps` time steps from rest), on all host cores.
+    Returns its timing and the reference velocity and apparent permeability the reduced-precision
+    results are compared with."""
+    import oracle
+    oracle.set_threads(os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    ref = oracle.run(oracle.equilibrium_state(19, field96.shape), field96.astype(np.float64), w["tau"], w["F"],
+                     (0, 0, 0), steps)
+    dt = time.perf_counter() - t0
+    _, u = oracle.moments(ref, w["F"], (0, 0, 0))
+    st = oracle.stats(ref, w["tau"], w["F"], (0, 0, 0))
+    cells = int(np.prod(field96.shape))
+    return {"mlups": cells * steps / dt / 1e6, "seconds": dt, "cores": oracle.get_threads(),
+            "sample": "%d FP64 oracle time steps of the 96^3 resampled field" % steps}, u, st["k_app"]
 
 
 def run_reference(args, w, rank):
@@ -236,6 +288,96 @@ def run_reference(args, w, rank):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def time_lattice(lat, inner, steps, warmup, stream):
+    """Warm up, then time `steps` bench steps (inner time steps + one FP64 reduction) with CUDA
+    events on the launching stream. Returns (ms per bench step, ms per time step of the step
+    kernel alone, last diagnostics)."""
+    import torch
+    for _ in range(warmup):
+        lat.step(inner)
+        lat.reduce()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    st = None
+    for a, b in evs:
+        a.record(stream)
+        lat.step(inner)
+        b.record(stream)
+        st = lat.reduce()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / steps, sum(a.elapsed_time(b) for a, b in evs) / (steps * inner), st
+
+
+def lattice_leg(w, field, storage, pattern, inner, steps, warmup, stream):
+    """GLUPS, step-kernel time and roofline fraction of one workload through the product API."""
+    import paper_2310_14746_gb300 as hb
+    n, q = w["n"], w["q"]
+    lat = hb.Lattice(q, n, n, n, storage, pattern)
+    lat.set_relaxation(w["tau"])
+    lat.set_force(*w["F"])
+    lat.set_porosity(field)
+    lat.init_equilibrium()
+    ms_step, kern_ms, st = time_lattice(lat, inner, steps, warmup, stream)
+    lat.close()
+    cells = n ** 3
+    bpl = 2 * q * hb.STORAGE_BYTES[storage] + 4
+    peak, kind = measured_hbm_peak()
+    achieved = bpl * cells / (kern_ms * 1e-3) / 1e9
+    return {"glups": cells * inner / (ms_step * 1e-3) / 1e9, "ms_per_step": ms_step, "kernel_ms": kern_ms,
+            "bytes_per_lup": bpl, "achieved_GBps": achieved, "frac": achieved / peak, "peak_kind": kind,
+            "k_app": st["k_app"], "mass_rel_drift": st["mass"] / cells - 1.0}
+
+
+def reduced_precision_leg(args, stream, with_oracle):
+    """The random-sphere workload: FP16 and BF16 deviation storage at 384^3 (throughput and roofline
+    at 80 B per lattice update), and at 96^3 on the same continuous geometry the velocity and
+    apparent-permeability error of FP32, FP16 and BF16 after 2000 steps against the FP64 oracle
+    (run on the host cores as the CPU baseline of this workload; skipped with_oracle=False)."""
+    import paper_2310_14746_gb300 as hb
+    w16 = WORKLOADS["d3q19_384_f16"]
+    field = make_field(w16)
+    out = {"workload": w16["desc"], "steps_per_bench_step": args.check_every}
+    for name, storage in (("f16", hb.HLBM_F16DEV), ("bf16", hb.HLBM_BF16DEV)):
+        out[name + "_384"] = lattice_leg(w16, field, storage, hb.HLBM_TWO_LATTICE, args.check_every,
+                                         args.leg_steps, 3, stream)
+    del field
+    err_steps = 2000
+    field96 = make_field(w16, render_n=96)
+    gpu = {}
+    for name, storage in (("f32", hb.HLBM_F32), ("f16", hb.HLBM_F16DEV), ("bf16", hb.HLBM_BF16DEV)):
+        lat = hb.Lattice(19, 96, 96, 96, storage, hb.HLBM_TWO_LATTICE)
+        lat.set_relaxation(w16["tau"])
+        lat.set_force(*w16["F"])
+        lat.set_porosity(field96)
+        lat.init_equilibrium()
+        lat.step(err_steps)
+        st = lat.reduce()
+        _, u = lat.moments()
+        lat.close()
+        gpu[name] = (u, st["k_app"])
+    if with_oracle:
+        timing, u_ref, k_ref = oracle_reference_96(w16, field96, err_steps)
+        scale = float(np.abs(u_ref).max())
+        out["error_96"] = {
+            name: {"velocity_rel_err": float(np.abs(u.astype(np.float64) - u_ref).max() / scale),
+                   "k_app_rel_err": abs(k - k_ref) / abs(k_ref)}
+            for name, (u, k) in gpu.items()}
+        out["error_96"]["reference"] = "FP64 oracle, 96^3, %d steps, k_app %.6g" % (err_steps, k_ref)
+        out["oracle_96"] = timing
+    return out
+
+
+def aa_leg(args, w, field, stream):
+    """The benchmark workload with in-place AA streaming, through the product API."""
+    import paper_2310_14746_gb300 as hb
+    return dict(lattice_leg(w, field, hb.HLBM_F32, hb.HLBM_AA, args.check_every, args.leg_steps, 3, stream),
+                workload="as the benchmark workload, in-place AA streaming (one population copy)")
+
 
 def adjoint_leg(n=128, nsteps=2000, every=45, period=32, ratio=0.3, tau=0.6, F=(1e-6, 0.0, 0.0)):
     """Gradient of the outflow flux w.r.t. varpi on the adjoint workload (128^3 regular spheres,
@@ -303,14 +445,31 @@ def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, 
     for rq in trace:
         t += float(rng.exponential(1.0 / rate))
         rq["arrival_s"] = t
-    res_b, info_b = sv.run_stream(trace, field_of, storage=hb.HLBM_F16DEV, mem_budget=budget_gb << 30, tol=tol)
-    res_p, info_p = sv.plain_loop(trace, field_of, tol=tol)
+    want_u = len(trace) <= 64  # final velocities kept on the host for the comparison
+    res_b, info_b = sv.run_stream(trace, field_of, storage=hb.HLBM_F16DEV, mem_budget=budget_gb << 30, tol=tol,
+                                  want_u=want_u)
+    res_p, info_p = sv.plain_loop(trace, field_of, tol=tol, want_u=want_u)
     kb = {r["tag"]: r["k_app"] for r in res_b}
     kp = {r["tag"]: r["k_app"] for r in res_p}
     kerr = max(abs(kb[k] - kp[k]) / abs(kp[k]) for k in kb if k in kp and kp[k] != 0)
+    uerr = None
+    if want_u:
+        ub = {r["tag"]: r["u"] for r in res_b}
+        uerr = max(float(np.abs(ub[r["tag"]] - r["u"]).max() / np.abs(r["u"]).max()) for r in res_p)
+    cells_of = {rq["id"]: rq["edge"] ** 3 for rq in trace}
+    lu_all = sum(r["steps"] * cells_of[r["tag"]] for r in res_b)
+    lu_low = sum(r["steps_low"] * cells_of[r["tag"]] for r in res_b)
     pb = sv.percentiles([r["latency_s"] for r in res_b])
     pp = sv.percentiles([r["latency_s"] for r in res_p])
     span_b = max(r["t_finish"] for r in res_b)
+    per_request = None
+    if len(trace) <= 32:
+        lp = {r["tag"]: r["latency_s"] for r in res_p}
+        per_request = [{"edge": cells_of[r["tag"]] ** (1 / 3), "steps": r["steps"], "steps_low": r["steps_low"],
+                        "latency_batched_s": r["latency_s"], "latency_plain_s": lp.get(r["tag"])}
+                       for r in sorted(res_b, key=lambda r: r["tag"])]
+        for e in per_request:
+            e["edge"] = int(round(e["edge"]))
     if dist is not None:  # whole-job throughput; tail latency as the worst rank's
         pb["p99_s"] = max_over_ranks(pb["p99_s"], dist, "cuda")
         pp["p99_s"] = max_over_ranks(pp["p99_s"], dist, "cuda")
@@ -328,6 +487,9 @@ def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, 
                       "mlups": sum_over_ranks(info_p["lattice_updates"] / info_p["elapsed_s"] / 1e6, dist, "cuda"),
                       "converged": sum(r["status"] == 0 for r in res_p)},
         "k_app_rel_diff_f16_batched_vs_f32_plain": kerr,
+        "velocity_rel_diff_batched_vs_f32_plain": uerr,
+        "lattice_update_share_16bit": lu_low / max(lu_all, 1),
+        "per_request": per_request,
         "steps": {"min": int(min(r["steps"] for r in res_b)), "max": int(max(r["steps"] for r in res_b))},
     }
 
@@ -414,10 +576,18 @@ def run_gpu(args, w, rank, world, local_rank):
     achieved = bytes_per_lup * cells / (kern_ms * 1e-3) / 1e9
     peak, peak_kind = measured_hbm_peak()
     kname = "stream_collide_d%dq%d_%s_%s" % (3 if q == 19 else 2, q, w["storage"], w["pattern"])
-    traffic = KERNEL_TRAFFIC_BYTES.get((kname, n))
+    traffic, traffic_note = kernel_traffic(kname, n)
+
+    aa = None
+    if not args.no_legs and w["pattern"] == "two" and w["storage"] == "f32":
+        aa = aa_leg(args, w, varpi, stream)
+
+    reduced = None
+    if not args.no_legs and rank == 0:
+        reduced = reduced_precision_leg(args, stream, with_oracle=(world == 1 and not args.no_cpu_baseline))
 
     adjoint = None
-    if not args.no_adjoint:
+    if not args.no_adjoint and not args.no_legs:
         adjoint = adjoint_leg()
 
     serving = None
@@ -430,8 +600,12 @@ def run_gpu(args, w, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         mlups, ksteps, dt, cores = oracle_mlups(w, varpi, budget_s=args.cpu_budget)
+        m1, s1, d1, _ = oracle_mlups(w, varpi, steps=1, threads=1)
         cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": "%d FP64 oracle time steps of the full %d^3 lattice (%.1f s)" % (ksteps, n, dt)}
+               "sample": "%d FP64 oracle time steps of the full %d^3 lattice (%.1f s)" % (ksteps, n, dt),
+               "cores_1": {"value": m1, "unit": "MLUPS", "cores": 1,
+                           "sample": "%d FP64 oracle time step of the full %d^3 lattice on one core (%.1f s)"
+                                     % (s1, n, d1)}}
 
     if rank == 0:
         line = {
@@ -442,13 +616,16 @@ def run_gpu(args, w, rank, world, local_rank):
                        "check_every": inner, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (%.2f GB streamed per time step)" % (bytes_per_lup * cells / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
+                         "kernel_source_hash": kernel_source_hash(), "peak_kind": peak_kind,
                          "kernel": kname, "kernel_ms": kern_ms, "bytes_per_lup": bytes_per_lup},
             "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "stats": {"k_app": st["k_app"], "mass_rel_drift": st["mass"] / cells - 1.0, "max_du": st["max_du"]},
+            "aa": aa,
+            "reduced_precision": reduced,
             "adjoint": adjoint,
             "serving": serving,
         }
@@ -473,6 +650,9 @@ def main():
                     help="replay this many requests of the seeded serving trace, batched vs plain (0: skip)")
     ap.add_argument("--serving-max-edge", type=int, default=128)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient leg")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the AA, reduced-precision and adjoint legs (the main line only)")
+    ap.add_argument("--leg-steps", type=int, default=5, help="timed bench steps of each lattice leg")
     args = ap.parse_args()
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)

@@ -83,12 +83,14 @@ class Server:
 
 
 def run_stream(trace, field_of, storage=HLBM_F16DEV, mem_budget=64 << 30, check_every=100, tol=1e-6,
-               max_steps=10 ** 6, tau=0.6, F=(1e-6, 0.0, 0.0), realtime=True):
+               max_steps=10 ** 6, tau=0.6, F=(1e-6, 0.0, 0.0), realtime=True, want_u=False, backfill=None):
     """Replay `trace` (dicts with id and arrival_s, sorted by arrival) through a server.
     Requests are submitted once their arrival time has passed (checked between rounds);
     latency = finish - arrival on the server's clock, which starts with the trace.
-    With realtime=False every request arrives at t = 0. Returns (results, info)."""
-    srv = Server(mem_budget, storage, check_every)
+    With realtime=False every request arrives at t = 0. want_u: each result carries its final
+    velocity as "u". backfill: the server's age-priority window (None: the library default).
+    Returns (results, info)."""
+    srv = Server(mem_budget, storage, check_every, backfill=backfill)
     t0 = time.perf_counter()  # the server clock started just before
     arrival = {}
     results = []
@@ -97,7 +99,8 @@ def run_stream(trace, field_of, storage=HLBM_F16DEV, mem_budget=64 << 30, check_
         now = time.perf_counter() - t0
         while k < len(trace) and (not realtime or trace[k]["arrival_s"] <= now):
             rq = trace[k]
-            rid = srv.submit(field_of(rq), tau=tau, F=F, tol=tol, max_steps=max_steps, tag=rq["id"])
+            rid = srv.submit(field_of(rq), tau=tau, F=F, tol=tol, max_steps=max_steps, tag=rq["id"],
+                             want_u=want_u)
             arrival[rid] = rq["arrival_s"] if realtime else 0.0
             k += 1
         a, w = srv.pump()
@@ -116,9 +119,9 @@ def run_stream(trace, field_of, storage=HLBM_F16DEV, mem_budget=64 << 30, check_
 
 
 def plain_loop(trace, field_of, tol=1e-6, max_steps=10 ** 6, tau=0.6, F=(1e-6, 0.0, 0.0), check_every=100,
-               realtime=True):
+               realtime=True, want_u=False):
     """One FP32 solve at a time, one launch per time step (no graphs, no batching).
-    Returns results with latency = finish - arrival."""
+    Returns results with latency = finish - arrival (and the final velocity as "u" with want_u)."""
     t0 = time.perf_counter()
     results = []
     lups = 0
@@ -148,8 +151,9 @@ def plain_loop(trace, field_of, tol=1e-6, max_steps=10 ** 6, tau=0.6, F=(1e-6, 0
                 break
         lups += steps * nx * ny * nz
         t_fin = time.perf_counter() - t0
+        u = lat.moments()[1] if want_u else None
         results.append({"tag": rq["id"], "status": status, "steps": steps, "k_app": st["k_app"],
-                        "latency_s": t_fin - (rq["arrival_s"] if realtime else 0.0), "nx": nx})
+                        "latency_s": t_fin - (rq["arrival_s"] if realtime else 0.0), "nx": nx, "u": u})
         lat.close()
     return results, {"lattice_updates": lups, "elapsed_s": time.perf_counter() - t0}
 
