@@ -16,7 +16,13 @@ from . import (HLBM_D3Q19, HLBM_F32, HLBM_HALFWAY_BOUNCE_BACK, HLBM_PERIODIC, HL
 class HBGKFluxGrad(torch.autograd.Function):
     """J = HBGKFluxGrad.apply(varpi, cfg). varpi: float32 CUDA tensor [nz, ny, nx] in [0, 1].
     cfg keys: tau, F (3-tuple), nsteps, ckpt_every (default 45), plane_x (default nx-1),
-    bc (3-tuple of 0 periodic / 1 wall), storage (default FP32), velset (default D3Q19)."""
+    bc (3-tuple of 0 periodic / 1 wall), storage (default FP32), velset (default D3Q19).
+
+    When varpi requires a gradient, forward runs the whole adjoint (forward sweep with
+    checkpoints, then the reverse sweep) eagerly and keeps dJ/dvarpi; backward only scales it.
+    The reverse sweep needs the forward checkpoints, so deferring it to backward would mean a
+    second forward run; a forward whose gradient is never used therefore pays the adjoint's
+    cost. With no gradient requested, forward runs the forward steps alone."""
 
     @staticmethod
     def forward(ctx, varpi, cfg):

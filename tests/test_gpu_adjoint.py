@@ -79,12 +79,40 @@ def test_autograd_function_matches_direct_call():
     assert float(J3.item()) == J2
 
 
+def _fd_derivative(J_at, v0, h):
+    """dJ/dvarpi at v0 from FP64 forward runs: nodes v0 +- h where both stay in [0, 1] (central),
+    else v0 + s h and v0 + 2 s h on the side that does (second-order one-sided). The lattice
+    holds varpi in FP32, so every stencil takes the spacing of the rounded values: the
+    three-point Lagrange derivative through J(v0) and the two nodes, exact for a quadratic."""
+    def node(dv):
+        return float(np.float32(v0 + dv)) - v0
+    if v0 - h >= 0 and v0 + h <= 1:
+        d1, d2 = h, -h
+    else:
+        s = -1.0 if v0 + h > 1 else 1.0
+        d1, d2 = s * h, 2 * s * h
+    a1, a2 = node(d1), node(d2)
+    l0 = -(a1 + a2) / (a1 * a2)
+    l1 = -a2 / (a1 * (a1 - a2))
+    l2 = -a1 / (a2 * (a2 - a1))
+    return l0 * J_at(0.0) + l1 * J_at(d1) + l2 * J_at(d2)
+
+
+def test_fd_derivative_stencils():
+    """The stencils are exact for a quadratic in the rounded coordinate."""
+    for v0 in (0.0, 1.0, float(np.float32(0.37)), float(np.float32(0.9993)), float(np.float32(3e-4))):
+        def J_at(dv):
+            x = float(np.float32(v0 + dv))
+            return 2.0 + 3.0 * x - 5.0 * x * x
+        assert abs(_fd_derivative(J_at, v0, 1e-3) - (3.0 - 10.0 * v0)) < 1e-9, v0
+
+
 def test_adjoint_fd_128_fp64_forwards():
     """Adjoint workload at full size: 128^3, regular spheres (period 32, r = 0.3 P),
     tau = 0.6, F = 1e-6, 2000 steps, checkpoint every 45 steps, FP32 gradient. Checked on
-    64 random cells against finite differences of FP64-storage forward runs (central
-    differences where varpi +- h stays in [0, 1], second-order one-sided ones at varpi = 0
-    or 1), h = 1e-3: within 1e-3 of the largest sampled |gradient|."""
+    64 random cells against finite differences of FP64-storage forward runs (h = 1e-3, three-point
+    stencils on the rounded spacing): within 1e-3 of the largest sampled |gradient| on every
+    cell, and within 1e-2 relative on every cell whose |gradient| exceeds 1e-2 of the largest."""
     n, nsteps, h = 128, 2000, 1e-3
     tau, F = 0.6, (1e-6, 0.0, 0.0)
     vp = inputs.regular_sphere_field(n, period=32, radius_ratio=0.3)
@@ -108,22 +136,22 @@ def test_adjoint_fd_128_fp64_forwards():
     fd, ad = [], []
     for c in cells:
         v0 = float(vp[c])
-        def Jd(dv):
+
+        def J_at(dv):
+            if dv == 0.0:
+                return J0
             f = vp.copy()
             f[c] = np.float32(v0 + dv)
             return J_of(f)
-        if v0 - h >= 0 and v0 + h <= 1:
-            # the perturbed values are rounded to FP32: difference by the actual spacing
-            ap = float(np.float32(v0 + h)) - v0
-            am = float(np.float32(v0 - h)) - v0
-            d = (Jd(h) - Jd(-h)) / (ap - am)
-        elif v0 + h > 1:
-            d = (3 * J0 - 4 * Jd(-h) + Jd(-2 * h)) / (2 * h)
-        else:
-            d = (-3 * J0 + 4 * Jd(h) - Jd(2 * h)) / (2 * h)
-        fd.append(d)
+        fd.append(_fd_derivative(J_at, v0, h))
         ad.append(float(grad[c]))
     fd, ad = np.array(fd), np.array(ad)
     fwd.close()
-    assert np.abs(fd).max() > 0
-    assert np.abs(fd - ad).max() <= 1e-3 * np.abs(fd).max(), (fd, ad)
+    scale = np.abs(fd).max()
+    assert scale > 0
+    big = np.abs(fd) > 1e-2 * scale
+    rel = np.abs(fd - ad)[big] / np.abs(fd)[big]
+    print("adjoint 128^3: max |fd - ad| / max |fd| = %.3g; per-cell relative (|fd| > 1e-2 max, %d cells) "
+          "max %.3g" % (np.abs(fd - ad).max() / scale, int(big.sum()), rel.max()))
+    assert np.abs(fd - ad).max() <= 1e-3 * scale, (fd, ad)
+    assert rel.max() <= 1e-2, (fd[big], ad[big])

@@ -156,14 +156,16 @@ def test_aa_periodic_bitwise(q, shape, storage):
     b.close()
 
 
-@pytest.mark.parametrize("storage,tol", [(hb.HLBM_F64, 1e-9), (hb.HLBM_F32, 1e-5)])
+@pytest.mark.parametrize("storage,tol", [(hb.HLBM_F64, 1e-10), (hb.HLBM_F32, 1e-5)])
 def test_config1_brinkman_channel(storage, tol, oracle):
     """D2Q9 channel 64x32, x periodic, half-way bounce-back walls in y, varpi = 0.9,
     F = 1e-6, tau = 0.8, 5000 steps: velocity vs the oracle, and the profile vs the
     continuous Brinkman solution of eq. targetEBTL (1.5e-2 relative L2).
-    The FP64 bound is set by the oracle: it keeps raw populations f ~ 0.1, so a velocity
-    of ~3e-6 formed from them carries ~1e-16 / 3e-6 ~ 1e-11 relative cancellation per
-    step; the GPU's FP64 deviations are the more precise side."""
+    The FP64 bound is set by the oracle: it keeps raw populations f ~ 0.1, so the ~1e-5
+    velocities formed from them carry cancellation error. Measured: the oracle drifts
+    2.2e-11 relative from the closed-form uniform-box recursion at this velocity scale over
+    5000 steps (test_oracle_flux.py), and the GPU's FP64 deviations differ from the oracle by
+    2.1e-11 here; the bound leaves a factor of about 5."""
     import math
     shape, bc = (1, 32, 64), (0, 1, 0)
     tau, varpi, g = 0.8, 0.9, 1e-6
@@ -175,7 +177,10 @@ def test_config1_brinkman_channel(storage, tol, oracle):
         _, u = lat.moments(f64=True)
         ref = oracle.run(oracle.equilibrium_state(9, shape), vp.astype(np.float64), tau, F, bc, 5000)
         _, ur = oracle.moments(ref, F, bc)
-        assert rel_inf(u, ur) < tol
+        err = rel_inf(u, ur)
+        print("config-1 channel, %s, pattern %d: velocity rel error vs oracle %.3g"
+              % (hb.STORAGE_NAMES[storage], pattern, err))
+        assert err < tol
         H = 32
         nu = (tau - 0.5) / 3
         lam = (1 - varpi) / tau
