@@ -412,9 +412,11 @@ def adjoint_leg(n=128, nsteps=2000, every=45, period=32, ratio=0.3, tau=0.6, F=(
             "grad_abs_max": float(grad.abs().max().item())}
 
 
-def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, world=1, dist=None):
+def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, world=1, dist=None,
+                capacity_requests=0):
     """Serving stream sample: the first n_requests of the seeded trace (edges up to max_edge).
-    1) capacity: all requests at t = 0 through the batched FP16 server -> solves/s;
+    1) capacity: all requests (or the first capacity_requests of them) at t = 0 through the
+       batched FP16 server -> solves/s;
     2) Poisson arrivals at 0.8x that capacity, replayed in real time through the batched server
        and through the plain FP32 loop (one solve at a time, one launch per step);
     returns p50/p99 time-to-steady-state of both, throughput, and the permeability difference
@@ -435,7 +437,8 @@ def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, 
 
     for rq in base:
         field_of(rq)
-    res0, info0 = sv.run_stream(base, field_of, storage=hb.HLBM_F16DEV, mem_budget=budget_gb << 30, tol=tol,
+    cap_set = base[:capacity_requests] if capacity_requests > 0 else base
+    res0, info0 = sv.run_stream(cap_set, field_of, storage=hb.HLBM_F16DEV, mem_budget=budget_gb << 30, tol=tol,
                                 realtime=False)
     cap = len(res0) / max(max(r["t_finish"] for r in res0), 1e-9)
     rate = 0.8 * cap
@@ -474,9 +477,17 @@ def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, 
         pb["p99_s"] = max_over_ranks(pb["p99_s"], dist, "cuda")
         pp["p99_s"] = max_over_ranks(pp["p99_s"], dist, "cuda")
         kerr = max_over_ranks(kerr, dist, "cuda")
+    by_edge = {}
+    lp_all = {r["tag"]: r["latency_s"] for r in res_p}
+    for e in sorted({rq["edge"] for rq in trace}):
+        tb = [r["latency_s"] for r in res_b if cells_of[r["tag"]] == e ** 3]
+        tp = [lp_all[r["tag"]] for r in res_b if cells_of[r["tag"]] == e ** 3 and r["tag"] in lp_all]
+        by_edge[str(e)] = {"n": len(tb), "batched": sv.percentiles(tb), "plain": sv.percentiles(tp)}
     return {
         "requests": len(trace), "edges": sorted({r["edge"] for r in trace}), "tol_max_du": tol,
-        "capacity_solves_per_s": cap, "arrival_rate_per_s": rate,
+        "capacity_solves_per_s": cap, "capacity_requests": len(cap_set), "arrival_rate_per_s": rate,
+        "by_edge": by_edge if len(trace) > 32 else None,
+        "lattice_updates": {"batched": int(lu_all), "low_precision": int(lu_low)},
         "batched_f16": {"p50_s": pb["p50_s"], "p99_s": pb["p99_s"],
                         "solves_per_s": sum_over_ranks(len(res_b) / span_b, dist, "cuda"),
                         "mlups": sum_over_ranks(info_b["lattice_updates"] / info_b["elapsed_s"] / 1e6, dist, "cuda"),
@@ -492,6 +503,22 @@ def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, 
         "per_request": per_request,
         "steps": {"min": int(min(r["steps"] for r in res_b)), "max": int(max(r["steps"] for r in res_b))},
     }
+
+
+def run_serving_only(args, rank, world, local_rank):
+    """Only the serving leg (for long traces): one JSON line with the serving object."""
+    import torch
+    from paper_2310_14746_gb300 import build
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local_rank)
+    build.build()
+    t0 = time.perf_counter()
+    serving = serving_leg(args.serving_requests, 2310147460 + 4, max_edge=args.serving_max_edge,
+                          rank=rank, world=world, capacity_requests=args.serving_capacity_requests)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "impl": "ours", "mode": "serving-only", "n_gpus": world,
+                          "wall_s": time.perf_counter() - t0, "serving": serving}), flush=True)
 
 
 def run_gpu(args, w, rank, world, local_rank):
@@ -649,6 +676,10 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=16,
                     help="replay this many requests of the seeded serving trace, batched vs plain (0: skip)")
     ap.add_argument("--serving-max-edge", type=int, default=128)
+    ap.add_argument("--serving-capacity-requests", type=int, default=0,
+                    help="measure the batched capacity on the first K requests only (0: all of them)")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the serving leg (long traces) and print its JSON object")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient leg")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the AA, reduced-precision and adjoint legs (the main line only)")
@@ -662,6 +693,8 @@ def main():
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w, rank)
+    elif args.serving_only:
+        run_serving_only(args, rank, world, local_rank)
     else:
         run_gpu(args, w, rank, world, local_rank)
 
