@@ -13,8 +13,9 @@
 //    loads (LD_HALVES); L1 serves the overlap between neighbouring threads;
 //  * stores: one 32-bit word per direction, packed by a single paired
 //    conversion.
-// The collision is the same FP32 function as the per-cell kernel, so both
-// kernels produce bit-identical states. A first version that passed the
+// The collision is the same function as the per-cell kernel, evaluated on
+// both cells at once with the paired FP32 instructions (lane type F2 of
+// lattice.cuh), so both kernels produce bit-identical states. A first version that passed the
 // x-shifted halves between lanes with shuffles (so that every load was one
 // aligned word) ran slower than the per-cell kernel: the extra loads of the
 // first and last lane of each row segment and the shuffle latency cost more
@@ -122,11 +123,14 @@ __device__ __forceinline__ void pair_gather(const Planes<const typename S::T, Q>
     }
 }
 
+#ifndef HLBM_PAIR_FX_BLOCKS
+#define HLBM_PAIR_FX_BLOCKS 4
+#endif
 template <int FORM>
 struct PairTraits {
     // the force-along-x form fits 64 registers (4 blocks per SM) with word loads; the
     // others take 80 (3 blocks) with 16-bit loads on the x-shifted directions
-    static constexpr int kMinBlocks = FORM == FORM_SHIFT_FX ? 4 : 3;
+    static constexpr int kMinBlocks = FORM == FORM_SHIFT_FX ? HLBM_PAIR_FX_BLOCKS : 3;
     static constexpr int kLoad = FORM == FORM_SHIFT_FX ? LD_WORDS : LD_HALVES;
 };
 
@@ -145,27 +149,30 @@ k_step_pair(Planes<const typename S::T, Q> fin, Planes<typename S::T, Q> fout, c
     const int xm1 = x0 == 0 ? g.nx - 1 : -1;
     const int xp2 = x0 + 2 >= g.nx ? -x0 : 2;
 
-    float d0[Q], d1[Q];
-    pair_gather<Q, S, PairTraits<FORM>::kLoad>(fin, cell, nb, xm1, xp2, d0, d1);
+    F2 d[Q];  // lane 0: cell x0, lane 1: cell x0 + 1
+    {
+        float d0[Q], d1[Q];
+        pair_gather<Q, S, PairTraits<FORM>::kLoad>(fin, cell, nb, xm1, xp2, d0, d1);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = F2(d0[i], d1[i]);
+    }
 
+    // each post-collision pair of values is stored as one 32-bit word as soon as it is final
+    const auto store = [&](int i, F2 v) {
+        const float2 f = v.split();
+        *reinterpret_cast<unsigned*>(fout.p[i] + cell) = P::pack(f.x, f.y);
+    };
     if (FORM == FORM_ANISO) {
         float2 v3[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) v3[a] = __ldg(reinterpret_cast<const float2*>(varpi3 + (size_t)a * g.N + cell));
-        collide_aniso<Q, float, S::scaled>(d0, v3[0].x, v3[1].x, v3[2].x, ph, s, inv_s);
-        collide_aniso<Q, float, S::scaled>(d1, v3[0].y, v3[1].y, v3[2].y, ph, s, inv_s);
+        collide_aniso<Q, F2, S::scaled>(d, F2(v3[0].x, v3[0].y), F2(v3[1].x, v3[1].y), F2(v3[2].x, v3[2].y), ph, s,
+                                        inv_s, store);
     } else {
         const float2 vp = __ldg(reinterpret_cast<const float2*>(varpi + cell));
-        if (FORM == FORM_DRAG) {
-            collide_drag<Q, float, S::scaled>(d0, vp.x, ph, s, inv_s);
-            collide_drag<Q, float, S::scaled>(d1, vp.y, ph, s, inv_s);
-        } else {
-            collide<Q, float, S::scaled, FORM == FORM_SHIFT_FX>(d0, vp.x, ph, s, inv_s);
-            collide<Q, float, S::scaled, FORM == FORM_SHIFT_FX>(d1, vp.y, ph, s, inv_s);
-        }
+        if (FORM == FORM_DRAG) collide_drag<Q, F2, S::scaled>(d, F2(vp.x, vp.y), ph, s, inv_s, store);
+        else collide<Q, F2, S::scaled, FORM == FORM_SHIFT_FX>(d, F2(vp.x, vp.y), ph, s, inv_s, store);
     }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) *reinterpret_cast<unsigned*>(fout.p[i] + cell) = P::pack(d0[i], d1[i]);
 }
 
 // Launch of the paired kernel; the caller has checked pair_applies().

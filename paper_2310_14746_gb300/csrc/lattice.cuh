@@ -11,6 +11,7 @@
 #include <cstddef>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 namespace hlbm {
 
@@ -304,8 +305,173 @@ __host__ inline Phys<C> make_phys(double tau, const double F[3]) {
     return p;
 }
 
-__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+// ---------------------------------------------------------------------------
+// Lane arithmetic of the collision. Every operation of the collision below is
+// written out and rounded on its own (a product is never contracted into a
+// following add, nothing is reassociated), so the collision is the same
+// sequence of IEEE operations whether a thread updates one cell (lane type
+// float or double) or two neighbouring cells at once (F2: the paired FP32
+// instructions add/sub/mul/fma .rn.f32x2 of sm_100-class GPUs, one issue slot
+// for both lanes, each lane rounded exactly as the scalar instruction). Every
+// step kernel therefore produces the same bits for a cell, and the paired
+// 16-bit kernels issue about half the floating-point instructions.
+// ---------------------------------------------------------------------------
+// All helpers are PTX instructions with an explicit rounding modifier. Measured
+// on GB300 (4M random operand triples): each paired instruction rounds every lane
+// exactly as the scalar instruction does, and a scalar multiply followed by a
+// scalar add is never fused; but a paired multiply whose result only feeds a
+// paired add or subtract is contracted into a paired fma by the code generator
+// (about 20 % of random x + a*b then differ from the separately rounded value).
+// The collision below is therefore written so that no product is added or
+// subtracted after rounding.
+__device__ __forceinline__ float add_(float a, float b) {
+    float d;
+    asm("add.rn.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float sub_(float a, float b) {
+    float d;
+    asm("sub.rn.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float mul_(float a, float b) {
+    float d;
+    asm("mul.rn.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float fma_(float a, float b, float c) {
+    float d;
+    asm("fma.rn.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double add_(double a, double b) {
+    double d;
+    asm("add.rn.f64 %0, %1, %2;" : "=d"(d) : "d"(a), "d"(b));
+    return d;
+}
+__device__ __forceinline__ double sub_(double a, double b) {
+    double d;
+    asm("sub.rn.f64 %0, %1, %2;" : "=d"(d) : "d"(a), "d"(b));
+    return d;
+}
+__device__ __forceinline__ double mul_(double a, double b) {
+    double d;
+    asm("mul.rn.f64 %0, %1, %2;" : "=d"(d) : "d"(a), "d"(b));
+    return d;
+}
+__device__ __forceinline__ double fma_(double a, double b, double c) {
+    double d;
+    asm("fma.rn.f64 %0, %1, %2, %3;" : "=d"(d) : "d"(a), "d"(b), "d"(c));
+    return d;
+}
+__device__ __forceinline__ double rcp_(double a) { return __drcp_rn(a); }
+
+// Two FP32 lanes in one 64-bit register pair (lane 0 = the lower cell of a pair).
+struct F2 {
+    unsigned long long v;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ explicit F2(float a) { asm("mov.b64 %0, {%1, %1};" : "=l"(v) : "f"(a)); }
+    __device__ __forceinline__ F2(float lo, float hi) { asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(lo), "f"(hi)); }
+    __device__ __forceinline__ float2 split() const {
+        float2 r;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+        return r;
+    }
+};
+__device__ __forceinline__ F2 add_(F2 a, F2 b) {
+    F2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 sub_(F2 a, F2 b) {
+    F2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 mul_(F2 a, F2 b) {
+    F2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 fma_(F2 a, F2 b, F2 c) {
+    F2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
+__device__ __forceinline__ F2 rcp_(F2 a) {
+    const float2 x = a.split();
+    return F2(__frcp_rn(x.x), __frcp_rn(x.y));
+}
+
+// Scalar type of a lane type; V(k) broadcasts a scalar to every lane.
+template <class V>
+struct Lane {
+    using S = V;
+};
+template <>
+struct Lane<F2> {
+    using S = float;
+};
+
+// sum_a c_a x_a for a direction with components in {-1, 0, 1} and at least one
+// +1: the +1 terms in axis order, then the -1 terms subtracted (no products).
+template <int CX, int CY, int CZ, class V>
+__device__ __forceinline__ V cdot(V x, V y, V z) {
+    static_assert(CX == 1 || CY == 1 || CZ == 1, "cdot needs a +1 component");
+    V r = CX == 1 ? x : (CY == 1 ? y : z);
+    if (CY == 1 && CX == 1) r = add_(r, y);
+    if (CZ == 1 && (CX == 1 || CY == 1)) r = add_(r, z);
+    if (CX == -1) r = sub_(r, x);
+    if (CY == -1) r = sub_(r, y);
+    if (CZ == -1) r = sub_(r, z);
+    return r;
+}
+template <int Q, int I, class V>
+__device__ __forceinline__ V cdot_i(V x, V y, V z) {
+    using L = Lat<Q>;
+    return cdot<L::cx(I), L::cy(I), L::cz(I), V>(x, y, z);
+}
+// The same for uniform scalars with a general sign pattern (force components).
+template <int Q, int I, class S>
+__device__ __forceinline__ S cdot_s(S x, S y, S z) {
+    using L = Lat<Q>;
+    S r = S(0);
+    if (L::cx(I) > 0) r = add_(r, x);
+    if (L::cx(I) < 0) r = sub_(r, x);
+    if (L::cy(I) > 0) r = add_(r, y);
+    if (L::cy(I) < 0) r = sub_(r, y);
+    if (L::cz(I) > 0) r = add_(r, z);
+    if (L::cz(I) < 0) r = sub_(r, z);
+    return r;
+}
+
+// Moments of the deviations for the collision: drho = sum d (index order) and
+// j = sum c d (per axis: from the first +1 direction, then in index order).
+template <int Q, int A, class V>
+__device__ __forceinline__ V axis_sum(const V* d) {
+    using L = Lat<Q>;
+    constexpr int first = A == 0 ? 1 : (Q == 9 ? 2 : (A == 1 ? 3 : 5));  // first direction with c_A = +1
+    V r = d[first];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (i == first) continue;
+        const int c = A == 0 ? L::cx(i) : (A == 1 ? L::cy(i) : L::cz(i));
+        if (c > 0) r = add_(r, d[i]);
+        if (c < 0) r = sub_(r, d[i]);
+    }
+    return r;
+}
+template <int Q, class V>
+__device__ __forceinline__ void moments_x(const V* d, V& drho, V& jx, V& jy, V& jz) {
+    V s = d[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) s = add_(s, d[i]);
+    drho = s;
+    jx = axis_sum<Q, 0>(d);
+    jy = axis_sum<Q, 1>(d);
+    jz = Q == 9 ? V(typename Lane<V>::S(0)) : axis_sum<Q, 2>(d);
+}
 
 // Zeroth and first moments of deviations d_i = g_i - w_i (Def. moments): drho =
 // sum d, j = sum c d (the weights carry no momentum); rho = 1 + drho and the
@@ -339,73 +505,140 @@ __device__ __forceinline__ void velocity(C jx, C jy, C jz, C inv_rho, const Phys
     uz = fma_(ph.Fz, h, jz * inv_rho);
 }
 
-// HBGK collision of one cell, in place on the deviations d (Sec. 3.2:
-// relaxation toward the Maxwellian at varpi*u; Guo's source built with u).
-// Opposite directions share the even part of the equilibrium and of the
-// source and differ in the sign of the odd part, so each pair costs one
+// Receiver of each final post-collision value: out(i, d_i) runs as soon as d_i
+// is known, so a kernel can store it at once instead of keeping all q values
+// live to the end (NoSink: the values only stay in d).
+struct NoSink {
+    template <class V>
+    __device__ __forceinline__ void operator()(int, V) const {}
+};
+
+// One opposite pair (I, opp(I)) of the collision: d_I = keep d_I + even + odd,
+// d_opp = keep d_opp + even - odd.
+template <int Q, int I, class V, class Sink>
+__device__ __forceinline__ void relax_pair(V* d, V keep, V even, V odd, Sink& out) {
+    constexpr int J = opp<Q>(I);
+    d[I] = add_(fma_(keep, d[I], even), odd);
+    d[J] = sub_(fma_(keep, d[J], even), odd);
+    out(I, d[I]);
+    out(J, d[J]);
+}
+
+// As relax_pair for an odd part that is a single product k (c.j): it enters
+// through an fma (k and -k), never as a product added afterwards.
+template <int Q, int I, class V, class Sink>
+__device__ __forceinline__ void relax_pair_prod(V* d, V keep, V even, V k, V nk, V cj, Sink& out) {
+    constexpr int J = opp<Q>(I);
+    d[I] = fma_(k, cj, fma_(keep, d[I], even));
+    d[J] = fma_(nk, cj, fma_(keep, d[J], even));
+    out(I, d[I]);
+    out(J, d[J]);
+}
+
+// sum_a c_a w_a x_a over the nonzero components of direction I as an fma chain
+// (c_a w_a is w_a or -w_a, an exact negation of an input), so no product is
+// added after it has been rounded.
+template <int Q, int I, class V>
+__device__ __forceinline__ V cdot_w(V wx, V wy, V wz, V nwx, V nwy, V nwz, V x, V y, V z) {
+    using L = Lat<Q>;
+    constexpr int cx = L::cx(I), cy = L::cy(I), cz = L::cz(I);
+    V r;
+    bool have = false;
+    if (cx != 0) {
+        r = mul_(cx > 0 ? wx : nwx, x);
+        have = true;
+    }
+    if (cy != 0) {
+        r = have ? fma_(cy > 0 ? wy : nwy, y, r) : mul_(cy > 0 ? wy : nwy, y);
+        have = true;
+    }
+    if (cz != 0) r = have ? fma_(cz > 0 ? wz : nwz, z, r) : mul_(cz > 0 ? wz : nwz, z);
+    return r;
+}
+
+// Compile-time loop over the pairs of a velocity set (each pair from its lower
+// index, which has a +1 component in both orderings).
+template <int Q, int I = 1, class F>
+__device__ __forceinline__ void for_pairs(F&& f) {
+    if constexpr (I < Q) {
+        if constexpr (opp<Q>(I) > I) f(std::integral_constant<int, I>{});
+        for_pairs<Q, I + 1>(f);
+    }
+}
+
+// HBGK collision of one cell (or of two, V = F2), in place on the deviations d
+// (Sec. 3.2: relaxation toward the Maxwellian at varpi*u; Guo's source built
+// with u). Opposite directions share the even part of the equilibrium and of
+// the source and differ in the sign of the odd part, so each pair costs one
 // evaluation:
 //   M_i - w_i = w_i [drho + rho (4.5 (c.v)^2 - 1.5 v.v)]  +-  3 w_i rho (c.v)
 //   S_i       = guo w_i [9 (c.u)(c.F) - 3 u.F]            +-  3 w_i guo (c.F)
 // and with rho (c.v) = varpi (c.j + c.F/2) the odd part of omega*M_i + S_i is
 //   k_i varpi (c.j) + (k_i varpi / 2 + g_i) (c.F).
-template <int Q, class C, bool SCALED = false, bool FX_ONLY = false>
-__device__ __forceinline__ void collide(C* d, C varpi, const Phys<C>& ph, C s = C(1), C inv_s = C(1)) {
+// c.u is formed as (c.j)/rho + (c.F)/(2 rho) and c.v as varpi (c.u). The code
+// generator may contract a paired multiply into a following paired add (it does
+// on GB300) but not a scalar one, so no product here is added or subtracted
+// after rounding: products only feed multiplies and fmas. That keeps the paired
+// and the scalar evaluations bit-identical.
+template <int Q, class V, bool SCALED = false, bool FX_ONLY = false, class Sink = NoSink>
+__device__ __forceinline__ void collide(V* d, V varpi, const Phys<typename Lane<V>::S>& ph,
+                                        typename Lane<V>::S s = 1, typename Lane<V>::S inv_s = 1, Sink out = Sink()) {
     // FX_ONLY: the caller guarantees F = (Fx, 0, 0); the terms with c.F = 0 drop out.
     // With SCALED the d are s * (f - w) on entry and exit; every term below
     // that adds into d carries the factor s (a power of two: exact).
     using L = Lat<Q>;
-    C drho_s, jxs, jys, jzs;  // sums in the units of d
-    moments<Q, C>(d, drho_s, jxs, jys, jzs);
-    const C drho = SCALED ? drho_s * inv_s : drho_s;
-    const C jx = SCALED ? jxs * inv_s : jxs, jy = SCALED ? jys * inv_s : jys, jz = SCALED ? jzs * inv_s : jzs;
-    const C rho = C(1) + drho;
-    const C inv_rho = C(1) / rho;
-    C ux, uy, uz;
-    velocity<C>(jx, jy, jz, inv_rho, ph, ux, uy, uz);
-    if (FX_ONLY) {
-        uy = jy * inv_rho;
-        uz = jz * inv_rho;
-    }
-    const C vx = varpi * ux, vy = varpi * uy, vz = varpi * uz;
-    const C rho_s = SCALED ? rho * s : rho;
-    const C A = fma_(-rho_s, C(1.5) * (vx * vx + vy * vy + vz * vz), drho_s);
-    const C uF3 = FX_ONLY ? C(3) * (ux * ph.Fx) : C(3) * (ux * ph.Fx + uy * ph.Fy + uz * ph.Fz);
-    const C r45 = C(4.5) * rho_s;
-    const C keep = C(1) - ph.omega;
-    const C guo_s = SCALED ? ph.guo * s : ph.guo;
+    using S = typename Lane<V>::S;
+    V drho_s, jxs, jys, jzs;  // sums in the units of d
+    moments_x<Q, V>(d, drho_s, jxs, jys, jzs);
+    const V rho = SCALED ? fma_(drho_s, V(inv_s), V(S(1))) : add_(V(S(1)), drho_s);
+    const V inv_rho = rcp_(rho);
+    const V im = SCALED ? mul_(inv_rho, V(inv_s)) : inv_rho;  // 1/rho in the units of d (exact scaling)
+    const V h = mul_(V(S(0.5)), inv_rho);
+    const V ux = fma_(V(ph.Fx), h, mul_(jxs, im));
+    const V uy = FX_ONLY ? mul_(jys, im) : fma_(V(ph.Fy), h, mul_(jys, im));
+    const V uz = FX_ONLY ? mul_(jzs, im) : fma_(V(ph.Fz), h, mul_(jzs, im));
+    const V rho_s = SCALED ? mul_(rho, V(s)) : rho;
+    const V uu = fma_(uz, uz, fma_(uy, uy, mul_(ux, ux)));
+    const V vv = mul_(mul_(varpi, varpi), uu);
+    const V A = fma_(mul_(rho_s, V(S(-1.5))), vv, drho_s);
+    // -3 u.F
+    const V nuF3 = FX_ONLY ? mul_(ux, V(mul_(S(-3), ph.Fx)))
+                           : mul_(V(S(-3)), fma_(uz, V(ph.Fz), fma_(uy, V(ph.Fy), mul_(ux, V(ph.Fx)))));
+    const V r45 = mul_(V(S(4.5)), rho_s);
+    const V keep = V(sub_(S(1), ph.omega));
+    const S guo_s = SCALED ? mul_(ph.guo, s) : ph.guo;
     {  // rest population
-        const C w = C(L::w(0));
-        d[0] = fma_(keep, d[0], fma_(ph.omega * w, A, -(guo_s * w) * uF3));
+        const S w = S(L::w(0));
+        d[0] = fma_(keep, d[0], fma_(V(mul_(ph.omega, w)), A, mul_(V(mul_(guo_s, w)), nuF3)));
+        out(0, d[0]);
     }
-    const C kv1 = ph.k1 * varpi, kv2 = ph.k2 * varpi;
-    const C g1 = SCALED ? ph.g1 * s : ph.g1, g2 = SCALED ? ph.g2 * s : ph.g2;
-    const C kvs1 = SCALED ? kv1 * s : kv1, kvs2 = SCALED ? kv2 * s : kv2;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const int j = opp<Q>(i);
-        if (j < i) continue;  // each pair once, from its lower index
-        const int c2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
-        const C cx = C(L::cx(i)), cy = C(L::cy(i)), cz = C(L::cz(i));
-        const C w = C(L::w(i));
-        const C cv = cx * vx + cy * vy + cz * vz;
-        const C cu = cx * ux + cy * uy + cz * uz;
-        // c.j in the units of d (scaled j when SCALED)
-        const C cj = cx * jxs + cy * jys + cz * jzs;
-        const C kv = c2 == 1 ? kv1 : kv2;
-        const C kvs = c2 == 1 ? kvs1 : kvs2;
-        const C g = c2 == 1 ? g1 : g2;
-        C even, odd;
-        if (FX_ONLY && L::cx(i) == 0) {  // c.F = 0
-            even = fma_(ph.omega * w, fma_(r45, cv * cv, A), -(guo_s * w) * uF3);
-            odd = kv * cj;
+    const V kv1 = mul_(V(ph.k1), varpi), kv2 = mul_(V(ph.k2), varpi);
+    const S g1 = SCALED ? mul_(ph.g1, s) : ph.g1, g2 = SCALED ? mul_(ph.g2, s) : ph.g2;
+    const V kvs1 = SCALED ? mul_(kv1, V(s)) : kv1, kvs2 = SCALED ? mul_(kv2, V(s)) : kv2;
+    for_pairs<Q>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        constexpr int c2 = L::cx(I) * L::cx(I) + L::cy(I) * L::cy(I) + L::cz(I) * L::cz(I);
+        const S w = S(L::w(I));
+        const V ow = V(mul_(ph.omega, w)), gw = V(mul_(guo_s, w));
+        const V cj = cdot_i<Q, I>(jxs, jys, jzs);  // c.j in the units of d
+        const V kv = c2 == 1 ? kv1 : kv2;
+        if (FX_ONLY && L::cx(I) == 0) {  // c.F = 0: the odd part is the product kv (c.j)
+            const V cu = mul_(cj, im);
+            const V cv = mul_(varpi, cu);
+            const V even = fma_(ow, fma_(r45, mul_(cv, cv), A), mul_(gw, nuF3));
+            const V nkv = mul_(V(c2 == 1 ? -ph.k1 : -ph.k2), varpi);
+            relax_pair_prod<Q, I>(d, keep, even, kv, nkv, cj, out);
         } else {
-            const C cF = FX_ONLY ? cx * ph.Fx : cx * ph.Fx + cy * ph.Fy + cz * ph.Fz;
-            even = fma_(ph.omega * w, fma_(r45, cv * cv, A), (guo_s * w) * fma_(C(9) * cu, cF, -uF3));
-            odd = fma_(kv, cj, fma_(kvs, C(0.5) * cF, g * cF));
+            const S cF = FX_ONLY ? (L::cx(I) > 0 ? ph.Fx : -ph.Fx) : cdot_s<Q, I>(ph.Fx, ph.Fy, ph.Fz);
+            const V cu = fma_(V(cF), h, mul_(cj, im));
+            const V cv = mul_(varpi, cu);
+            const V kvs = c2 == 1 ? kvs1 : kvs2;
+            const S g = c2 == 1 ? g1 : g2;
+            const V even = fma_(ow, fma_(r45, mul_(cv, cv), A), mul_(gw, fma_(mul_(V(S(9)), cu), V(cF), nuF3)));
+            const V odd = fma_(kv, cj, fma_(kvs, V(mul_(S(0.5), cF)), V(mul_(g, cF))));
+            relax_pair<Q, I>(d, keep, even, odd, out);
         }
-        d[i] = fma_(keep, d[i], even) + odd;
-        d[j] = fma_(keep, d[j], even) - odd;
-    }
+    });
 }
 
 // Explicit-drag form of the homogenization (Sec. 3.3, eq. momentumHLBM): the
@@ -414,104 +647,114 @@ __device__ __forceinline__ void collide(C* d, C varpi, const Phys<C>& ph, C s = 
 // velocity of the total force, u = (j + F/2) / (rho (1 + lam/2)). With
 // h = 1/(1 + lam/2), rho (c.u) = h (c.j + c.F/2) and c.G = c.F - lam rho (c.u),
 // so the odd part of omega*M_i + S_i is kk (c.j) + (kk/2 + g)(c.F) with
-// kk = (k - g lam) h: the same fma shape as the shift form.
-template <int Q, class C, bool SCALED = false>
-__device__ __forceinline__ void collide_drag(C* d, C varpi, const Phys<C>& ph, C s = C(1), C inv_s = C(1)) {
+// kk = (k - g lam) h: the same fma shape as the shift form (and the same rule:
+// no product is added after rounding).
+template <int Q, class V, bool SCALED = false, class Sink = NoSink>
+__device__ __forceinline__ void collide_drag(V* d, V varpi, const Phys<typename Lane<V>::S>& ph,
+                                             typename Lane<V>::S s = 1, typename Lane<V>::S inv_s = 1,
+                                             Sink out = Sink()) {
     using L = Lat<Q>;
-    C drho_s, jxs, jys, jzs;
-    moments<Q, C>(d, drho_s, jxs, jys, jzs);
-    const C drho = SCALED ? drho_s * inv_s : drho_s;
-    const C jx = SCALED ? jxs * inv_s : jxs, jy = SCALED ? jys * inv_s : jys, jz = SCALED ? jzs * inv_s : jzs;
-    const C rho = C(1) + drho;
-    const C lam = (C(1) - varpi) * ph.omega;
-    const C h = C(1) / fma_(C(0.5), lam, C(1));
-    C ux, uy, uz;
-    velocity<C>(jx, jy, jz, h / rho, ph, ux, uy, uz);
-    const C lr = -lam * rho;
-    const C Gx = fma_(lr, ux, ph.Fx), Gy = fma_(lr, uy, ph.Fy), Gz = fma_(lr, uz, ph.Fz);
-    const C rho_s = SCALED ? rho * s : rho;
-    const C A = fma_(-rho_s, C(1.5) * (ux * ux + uy * uy + uz * uz), drho_s);
-    const C uG3 = C(3) * (ux * Gx + uy * Gy + uz * Gz);
-    const C r45 = C(4.5) * rho_s;
-    const C keep = C(1) - ph.omega;
-    const C guo_s = SCALED ? ph.guo * s : ph.guo;
+    using S = typename Lane<V>::S;
+    V drho_s, jxs, jys, jzs;
+    moments_x<Q, V>(d, drho_s, jxs, jys, jzs);
+    const V rho = SCALED ? fma_(drho_s, V(inv_s), V(S(1))) : add_(V(S(1)), drho_s);
+    const V lam = mul_(sub_(V(S(1)), varpi), V(ph.omega));
+    const V nlam = mul_(sub_(varpi, V(S(1))), V(ph.omega));  // -lam, exactly
+    const V h = rcp_(fma_(V(S(0.5)), lam, V(S(1))));
+    const V hr = mul_(h, rcp_(rho));
+    const V hm = SCALED ? mul_(hr, V(inv_s)) : hr;  // in the units of d (exact scaling)
+    const V hh = mul_(V(S(0.5)), hr);
+    const V ux = fma_(V(ph.Fx), hh, mul_(jxs, hm));
+    const V uy = fma_(V(ph.Fy), hh, mul_(jys, hm));
+    const V uz = fma_(V(ph.Fz), hh, mul_(jzs, hm));
+    const V nlr = mul_(nlam, rho);  // -lam rho
+    const V Gx = fma_(nlr, ux, V(ph.Fx)), Gy = fma_(nlr, uy, V(ph.Fy)), Gz = fma_(nlr, uz, V(ph.Fz));
+    const V rho_s = SCALED ? mul_(rho, V(s)) : rho;
+    const V uu = fma_(uz, uz, fma_(uy, uy, mul_(ux, ux)));
+    const V A = fma_(mul_(rho_s, V(S(-1.5))), uu, drho_s);
+    const V nuG3 = mul_(V(S(-3)), fma_(uz, Gz, fma_(uy, Gy, mul_(ux, Gx))));
+    const V r45 = mul_(V(S(4.5)), rho_s);
+    const V keep = V(sub_(S(1), ph.omega));
+    const S guo_s = SCALED ? mul_(ph.guo, s) : ph.guo;
     {
-        const C w = C(L::w(0));
-        d[0] = fma_(keep, d[0], fma_(ph.omega * w, A, -(guo_s * w) * uG3));
+        const S w = S(L::w(0));
+        d[0] = fma_(keep, d[0], fma_(V(mul_(ph.omega, w)), A, mul_(V(mul_(guo_s, w)), nuG3)));
+        out(0, d[0]);
     }
-    const C kk1 = fma_(-ph.g1, lam, ph.k1) * h, kk2 = fma_(-ph.g2, lam, ph.k2) * h;
-    const C g1 = SCALED ? ph.g1 * s : ph.g1, g2 = SCALED ? ph.g2 * s : ph.g2;
-    const C kks1 = SCALED ? kk1 * s : kk1, kks2 = SCALED ? kk2 * s : kk2;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const int j = opp<Q>(i);
-        if (j < i) continue;
-        const int c2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
-        const C cx = C(L::cx(i)), cy = C(L::cy(i)), cz = C(L::cz(i));
-        const C w = C(L::w(i));
-        const C cu = cx * ux + cy * uy + cz * uz;
-        const C cG = cx * Gx + cy * Gy + cz * Gz;
-        const C cF = cx * ph.Fx + cy * ph.Fy + cz * ph.Fz;
-        const C cj = cx * jxs + cy * jys + cz * jzs;
-        const C kk = c2 == 1 ? kk1 : kk2;
-        const C kks = c2 == 1 ? kks1 : kks2;
-        const C g = c2 == 1 ? g1 : g2;
-        const C even = fma_(ph.omega * w, fma_(r45, cu * cu, A), (guo_s * w) * fma_(C(9) * cu, cG, -uG3));
-        const C odd = fma_(kk, cj, fma_(kks, C(0.5) * cF, g * cF));
-        d[i] = fma_(keep, d[i], even) + odd;
-        d[j] = fma_(keep, d[j], even) - odd;
-    }
+    const V kk1 = mul_(fma_(V(-ph.g1), lam, V(ph.k1)), h), kk2 = mul_(fma_(V(-ph.g2), lam, V(ph.k2)), h);
+    const S g1 = SCALED ? mul_(ph.g1, s) : ph.g1, g2 = SCALED ? mul_(ph.g2, s) : ph.g2;
+    const V kks1 = SCALED ? mul_(kk1, V(s)) : kk1, kks2 = SCALED ? mul_(kk2, V(s)) : kk2;
+    for_pairs<Q>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        constexpr int c2 = L::cx(I) * L::cx(I) + L::cy(I) * L::cy(I) + L::cz(I) * L::cz(I);
+        const S w = S(L::w(I));
+        const V ow = V(mul_(ph.omega, w)), gw = V(mul_(guo_s, w));
+        const V cu = cdot_i<Q, I>(ux, uy, uz);
+        const V cG = cdot_i<Q, I>(Gx, Gy, Gz);
+        const V cj = cdot_i<Q, I>(jxs, jys, jzs);
+        const S cF = cdot_s<Q, I>(ph.Fx, ph.Fy, ph.Fz);
+        const V kk = c2 == 1 ? kk1 : kk2;
+        const V kks = c2 == 1 ? kks1 : kks2;
+        const S g = c2 == 1 ? g1 : g2;
+        const V even = fma_(ow, fma_(r45, mul_(cu, cu), A), mul_(gw, fma_(mul_(V(S(9)), cu), cG, nuG3)));
+        const V odd = fma_(kk, cj, fma_(kks, V(mul_(S(0.5), cF)), V(mul_(g, cF))));
+        relax_pair<Q, I>(d, keep, even, odd, out);
+    });
 }
 
 // Anisotropic (diagonal-tensor) porosity control: the Maxwellian at
 // v = (vx ux, vy uy, vz uz), a per-axis drag nu/K_a. As collide(), with the
-// odd part k (c.(varpi o j)) + (k/2 c.(varpi o F) + g c.F).
-template <int Q, class C, bool SCALED = false>
-__device__ __forceinline__ void collide_aniso(C* d, C wx, C wy, C wz, const Phys<C>& ph, C s = C(1), C inv_s = C(1)) {
+// odd part k (c.(varpi o j)) + (k/2 c.(varpi o F) + g c.F); the weighted dot
+// products are fma chains.
+template <int Q, class V, bool SCALED = false, class Sink = NoSink>
+__device__ __forceinline__ void collide_aniso(V* d, V wx, V wy, V wz, const Phys<typename Lane<V>::S>& ph,
+                                              typename Lane<V>::S s = 1, typename Lane<V>::S inv_s = 1,
+                                              Sink out = Sink()) {
     using L = Lat<Q>;
-    C drho_s, jxs, jys, jzs;
-    moments<Q, C>(d, drho_s, jxs, jys, jzs);
-    const C drho = SCALED ? drho_s * inv_s : drho_s;
-    const C jx = SCALED ? jxs * inv_s : jxs, jy = SCALED ? jys * inv_s : jys, jz = SCALED ? jzs * inv_s : jzs;
-    const C rho = C(1) + drho;
-    const C inv_rho = C(1) / rho;
-    C ux, uy, uz;
-    velocity<C>(jx, jy, jz, inv_rho, ph, ux, uy, uz);
-    const C vx = wx * ux, vy = wy * uy, vz = wz * uz;
-    const C rho_s = SCALED ? rho * s : rho;
-    const C A = fma_(-rho_s, C(1.5) * (vx * vx + vy * vy + vz * vz), drho_s);
-    const C uF3 = C(3) * (ux * ph.Fx + uy * ph.Fy + uz * ph.Fz);
-    const C r45 = C(4.5) * rho_s;
-    const C keep = C(1) - ph.omega;
-    const C guo_s = SCALED ? ph.guo * s : ph.guo;
+    using S = typename Lane<V>::S;
+    V drho_s, jxs, jys, jzs;
+    moments_x<Q, V>(d, drho_s, jxs, jys, jzs);
+    const V rho = SCALED ? fma_(drho_s, V(inv_s), V(S(1))) : add_(V(S(1)), drho_s);
+    const V inv_rho = rcp_(rho);
+    const V im = SCALED ? mul_(inv_rho, V(inv_s)) : inv_rho;
+    const V h = mul_(V(S(0.5)), inv_rho);
+    const V ux = fma_(V(ph.Fx), h, mul_(jxs, im));
+    const V uy = fma_(V(ph.Fy), h, mul_(jys, im));
+    const V uz = fma_(V(ph.Fz), h, mul_(jzs, im));
+    const V nwx = sub_(V(S(0)), wx), nwy = sub_(V(S(0)), wy), nwz = sub_(V(S(0)), wz);
+    const V rho_s = SCALED ? mul_(rho, V(s)) : rho;
+    const V vx = mul_(wx, ux), vy = mul_(wy, uy), vz = mul_(wz, uz);
+    const V vv = fma_(vz, vz, fma_(vy, vy, mul_(vx, vx)));
+    const V A = fma_(mul_(rho_s, V(S(-1.5))), vv, drho_s);
+    const V nuF3 = mul_(V(S(-3)), fma_(uz, V(ph.Fz), fma_(uy, V(ph.Fy), mul_(ux, V(ph.Fx)))));
+    const V r45 = mul_(V(S(4.5)), rho_s);
+    const V keep = V(sub_(S(1), ph.omega));
+    const S guo_s = SCALED ? mul_(ph.guo, s) : ph.guo;
     {
-        const C w = C(L::w(0));
-        d[0] = fma_(keep, d[0], fma_(ph.omega * w, A, -(guo_s * w) * uF3));
+        const S w = S(L::w(0));
+        d[0] = fma_(keep, d[0], fma_(V(mul_(ph.omega, w)), A, mul_(V(mul_(guo_s, w)), nuF3)));
+        out(0, d[0]);
     }
-    const C pjx = wx * jxs, pjy = wy * jys, pjz = wz * jzs;             // varpi o j (units of d)
-    const C hFx = C(0.5) * wx * ph.Fx, hFy = C(0.5) * wy * ph.Fy, hFz = C(0.5) * wz * ph.Fz;
-    const C g1 = SCALED ? ph.g1 * s : ph.g1, g2 = SCALED ? ph.g2 * s : ph.g2;
-    const C ks1 = SCALED ? ph.k1 * s : ph.k1, ks2 = SCALED ? ph.k2 * s : ph.k2;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const int j = opp<Q>(i);
-        if (j < i) continue;
-        const int c2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
-        const C cx = C(L::cx(i)), cy = C(L::cy(i)), cz = C(L::cz(i));
-        const C w = C(L::w(i));
-        const C cv = cx * vx + cy * vy + cz * vz;
-        const C cu = cx * ux + cy * uy + cz * uz;
-        const C cF = cx * ph.Fx + cy * ph.Fy + cz * ph.Fz;
-        const C cpj = cx * pjx + cy * pjy + cz * pjz;
-        const C cpF = cx * hFx + cy * hFy + cz * hFz;
-        const C k = c2 == 1 ? ph.k1 : ph.k2;
-        const C ks = c2 == 1 ? ks1 : ks2;
-        const C g = c2 == 1 ? g1 : g2;
-        const C even = fma_(ph.omega * w, fma_(r45, cv * cv, A), (guo_s * w) * fma_(C(9) * cu, cF, -uF3));
-        const C odd = fma_(k, cpj, fma_(ks, cpF, g * cF));
-        d[i] = fma_(keep, d[i], even) + odd;
-        d[j] = fma_(keep, d[j], even) - odd;
-    }
+    const V hFx = V(mul_(S(0.5), ph.Fx)), hFy = V(mul_(S(0.5), ph.Fy)), hFz = V(mul_(S(0.5), ph.Fz));
+    const S g1 = SCALED ? mul_(ph.g1, s) : ph.g1, g2 = SCALED ? mul_(ph.g2, s) : ph.g2;
+    const S ks1 = SCALED ? mul_(ph.k1, s) : ph.k1, ks2 = SCALED ? mul_(ph.k2, s) : ph.k2;
+    for_pairs<Q>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        constexpr int c2 = L::cx(I) * L::cx(I) + L::cy(I) * L::cy(I) + L::cz(I) * L::cz(I);
+        const S w = S(L::w(I));
+        const V ow = V(mul_(ph.omega, w)), gw = V(mul_(guo_s, w));
+        const V cv = cdot_w<Q, I>(wx, wy, wz, nwx, nwy, nwz, ux, uy, uz);
+        const V cu = cdot_i<Q, I>(ux, uy, uz);
+        const S cF = cdot_s<Q, I>(ph.Fx, ph.Fy, ph.Fz);
+        const V cpj = cdot_w<Q, I>(wx, wy, wz, nwx, nwy, nwz, jxs, jys, jzs);  // c.(varpi o j), units of d
+        const V cpF = cdot_w<Q, I>(wx, wy, wz, nwx, nwy, nwz, hFx, hFy, hFz);  // c.(varpi o F)/2
+        const S k = c2 == 1 ? ph.k1 : ph.k2;
+        const S ks = c2 == 1 ? ks1 : ks2;
+        const S g = c2 == 1 ? g1 : g2;
+        const V even = fma_(ow, fma_(r45, mul_(cv, cv), A), mul_(gw, fma_(mul_(V(S(9)), cu), V(cF), nuF3)));
+        const V odd = fma_(V(k), cpj, fma_(V(ks), cpF, V(mul_(g, cF))));
+        relax_pair<Q, I>(d, keep, even, odd, out);
+    });
 }
 
 // Velocity seen by the collision of either form: u = (j + F/2)/rho for the

@@ -171,20 +171,22 @@ __device__ __forceinline__ void advance_pair(const DevSlot& sl, int k, int x0, i
     const Nbr<int> nb(g, x0, y, z);
     const int xm1 = x0 == 0 ? g.nx - 1 : -1;
     const int xp2 = x0 + 2 >= g.nx ? -x0 : 2;
-    float d0[19], d1[19];
+    F2 d[19];  // lane 0: cell x0, lane 1: cell x0 + 1
     const float2 vp = __ldg(reinterpret_cast<const float2*>(sl.varpi + cell));
     const Phys<float> ph = sl.ph;
-    if (FX) {  // force along x (the slot's fx_only)
-        pair_gather<19, S, LD_WORDS>(fin, cell, nb, xm1, xp2, d0, d1);
-        collide<19, float, S::scaled, true>(d0, vp.x, ph, sl.scale, sl.inv_scale);
-        collide<19, float, S::scaled, true>(d1, vp.y, ph, sl.scale, sl.inv_scale);
-    } else {
-        pair_gather<19, S, LD_HALVES>(fin, cell, nb, xm1, xp2, d0, d1);
-        collide<19, float, S::scaled, false>(d0, vp.x, ph, sl.scale, sl.inv_scale);
-        collide<19, float, S::scaled, false>(d1, vp.y, ph, sl.scale, sl.inv_scale);
-    }
+    {
+        float d0[19], d1[19];
+        if (FX) pair_gather<19, S, LD_WORDS>(fin, cell, nb, xm1, xp2, d0, d1);
+        else pair_gather<19, S, LD_HALVES>(fin, cell, nb, xm1, xp2, d0, d1);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) *reinterpret_cast<unsigned*>(fout + (i * N + cell)) = P::pack(d0[i], d1[i]);
+        for (int i = 0; i < 19; ++i) d[i] = F2(d0[i], d1[i]);
+    }
+    const auto store = [&](int i, F2 v) {  // one 32-bit word per direction, stored once final
+        const float2 f = v.split();
+        *reinterpret_cast<unsigned*>(fout + (i * N + cell)) = P::pack(f.x, f.y);
+    };
+    if (FX) collide<19, F2, S::scaled, true>(d, F2(vp.x, vp.y), ph, sl.scale, sl.inv_scale, store);  // fx_only
+    else collide<19, F2, S::scaled, false>(d, F2(vp.x, vp.y), ph, sl.scale, sl.inv_scale, store);
 }
 
 // q = n / d and r = n % d for 0 <= n < 2^21, d >= 1 (a slot has fewer tiles): a float-reciprocal
