@@ -91,6 +91,8 @@ WORKLOADS = {
                           period=32, ratio=0.3, desc="as d3q19_256_f32 with FP64 storage and arithmetic"),
     "d3q19_256_f16": dict(q=19, n=256, storage="f16", pattern="two", tau=0.6, F=(1e-6, 0.0, 0.0),
                           period=32, ratio=0.3, desc="as d3q19_256_f32 with FP16 deviation storage"),
+    "d3q19_256_bf16": dict(q=19, n=256, storage="bf16", pattern="two", tau=0.6, F=(1e-6, 0.0, 0.0),
+                           period=32, ratio=0.3, desc="as d3q19_256_f32 with BF16 deviation storage"),
     "d3q19_384_f16": dict(q=19, n=384, storage="f16", pattern="two", tau=0.6, F=(1e-6, 0.0, 0.0),
                           field="boolean",
                           desc="D3Q19 HBGK 384^3 random periodic Boolean sphere matrix (seeded, radius "

@@ -75,13 +75,14 @@ k_step(Planes<const typename S::T, Q> fin, Planes<typename S::T, Q> fout, const 
     const bool aniso = FORM == FORM_ANISO || (FORM == FORM_AUTO && varpi3);
     if (aniso) {  // diagonal porosity tensor [3][cells]
         collide_aniso<Q, C, S::scaled>(d, C(__ldg(varpi3 + cell)), C(__ldg(varpi3 + (I)g.N + cell)),
-                                       C(__ldg(varpi3 + 2 * (I)g.N + cell)), ph, s, inv_s);
+                                       C(__ldg(varpi3 + 2 * (I)g.N + cell)), ph, s, inv_s, WriteBack<C>{d});
     } else {
         const C vp = C(__ldg(varpi + cell));
-        if (FORM == FORM_DRAG || (FORM == FORM_AUTO && drag)) collide_drag<Q, C, S::scaled>(d, vp, ph, s, inv_s);
+        if (FORM == FORM_DRAG || (FORM == FORM_AUTO && drag))
+            collide_drag<Q, C, S::scaled>(d, vp, ph, s, inv_s, WriteBack<C>{d});
         else if (FORM == FORM_SHIFT_FX || (FORM == FORM_AUTO && fx_only))
-            collide<Q, C, S::scaled, true>(d, vp, ph, s, inv_s);
-        else collide<Q, C, S::scaled, false>(d, vp, ph, s, inv_s);
+            collide<Q, C, S::scaled, true>(d, vp, ph, s, inv_s, WriteBack<C>{d});
+        else collide<Q, C, S::scaled, false>(d, vp, ph, s, inv_s, WriteBack<C>{d});
     }
 
 #pragma unroll

@@ -123,6 +123,69 @@ __device__ __forceinline__ void pair_gather(const Planes<const typename S::T, Q>
     }
 }
 
+// The same gather keeping each direction's pair as one 32-bit word (lane 0 in
+// the low half): 19 registers instead of 38, unpacked exactly where used.
+template <int Q, class S, int LD>
+__device__ __forceinline__ void pair_gather_words(const Planes<const typename S::T, Q>& fin, int cell,
+                                                  const Nbr<int>& nb, int xm1, int xp2, unsigned* w) {
+    using L = Lat<Q>;
+    using T = typename S::T;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        int o = 0;  // y/z part of the pull offset
+        if (L::cy(i) > 0) o += nb.oym;
+        if (L::cy(i) < 0) o += nb.oyp;
+        if (L::cz(i) > 0) o += nb.ozm;
+        if (L::cz(i) < 0) o += nb.ozp;
+        const T* row = fin.p[i] + (cell + o);
+        if (L::cx(i) == 0) {
+            w[i] = __ldg(reinterpret_cast<const unsigned*>(row));
+        } else if (LD == LD_WORDS) {
+            const unsigned b = __ldg(reinterpret_cast<const unsigned*>(row));
+            w[i] = L::cx(i) > 0 ? __byte_perm(__ldg(reinterpret_cast<const unsigned*>(row + (xm1 - 1))), b, 0x5432)
+                                : __byte_perm(b, __ldg(reinterpret_cast<const unsigned*>(row + xp2)), 0x5432);
+        } else {
+            const unsigned short* r16 = reinterpret_cast<const unsigned short*>(row);
+            const unsigned lo = L::cx(i) > 0 ? __ldg(r16 + xm1) : __ldg(r16 + 1);  // sources x0 -+ 1
+            const unsigned hi = L::cx(i) > 0 ? __ldg(r16) : __ldg(r16 + xp2);      // sources x0, x0 + 2
+            w[i] = lo | (hi << 16);
+        }
+    }
+}
+
+// Exact unpack of a 16-bit pair word to two FP32 lanes, as an instruction
+// sequence the compiler does not merge between uses: a population is read
+// twice (moments, then relaxation), and unpacking it again is cheaper than
+// keeping both FP32 values live across the collision.
+template <class S>
+__device__ __forceinline__ F2 unpack_each_use(unsigned w);
+template <>
+__device__ __forceinline__ F2 unpack_each_use<StoreF16>(unsigned w) {
+    F2 r;
+    asm volatile(
+        "{\n\t.reg .b16 l16, h16;\n\t.reg .f32 lo, hi;\n\tmov.b32 {l16, h16}, %1;\n\t"
+        "cvt.f32.f16 lo, l16;\n\tcvt.f32.f16 hi, h16;\n\tmov.b64 %0, {lo, hi};\n\t}"
+        : "=l"(r.v) : "r"(w));
+    return r;
+}
+template <>
+__device__ __forceinline__ F2 unpack_each_use<StoreBF16>(unsigned w) {
+    F2 r;
+    asm volatile(
+        "{\n\t.reg .b32 lo, hi;\n\tshl.b32 lo, %1, 16;\n\tand.b32 hi, %1, 0xffff0000;\n\t"
+        "mov.b64 %0, {lo, hi};\n\t}"
+        : "=l"(r.v) : "r"(w));
+    return r;
+}
+
+// Populations of a cell pair held as the loaded 32-bit words (lane 0 in the
+// low half); d[i] unpacks direction i to the two FP32 lanes on each use.
+template <class S, int Q>
+struct PackedPairs {
+    unsigned w[Q];
+    __device__ __forceinline__ F2 operator[](int i) const { return unpack_each_use<S>(w[i]); }
+};
+
 #ifndef HLBM_PAIR_FX_BLOCKS
 #define HLBM_PAIR_FX_BLOCKS 4
 #endif
@@ -149,13 +212,8 @@ k_step_pair(Planes<const typename S::T, Q> fin, Planes<typename S::T, Q> fout, c
     const int xm1 = x0 == 0 ? g.nx - 1 : -1;
     const int xp2 = x0 + 2 >= g.nx ? -x0 : 2;
 
-    F2 d[Q];  // lane 0: cell x0, lane 1: cell x0 + 1
-    {
-        float d0[Q], d1[Q];
-        pair_gather<Q, S, PairTraits<FORM>::kLoad>(fin, cell, nb, xm1, xp2, d0, d1);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) d[i] = F2(d0[i], d1[i]);
-    }
+    PackedPairs<S, Q> d;  // the loaded words; lane 0: cell x0, lane 1: cell x0 + 1
+    pair_gather_words<Q, S, PairTraits<FORM>::kLoad>(fin, cell, nb, xm1, xp2, d.w);
 
     // each post-collision pair of values is stored as one 32-bit word as soon as it is final
     const auto store = [&](int i, F2 v) {

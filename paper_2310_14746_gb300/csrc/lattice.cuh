@@ -448,8 +448,8 @@ __device__ __forceinline__ S cdot_s(S x, S y, S z) {
 
 // Moments of the deviations for the collision: drho = sum d (index order) and
 // j = sum c d (per axis: from the first +1 direction, then in index order).
-template <int Q, int A, class V>
-__device__ __forceinline__ V axis_sum(const V* d) {
+template <int Q, int A, class V, class Pop>
+__device__ __forceinline__ V axis_sum(const Pop& d) {
     using L = Lat<Q>;
     constexpr int first = A == 0 ? 1 : (Q == 9 ? 2 : (A == 1 ? 3 : 5));  // first direction with c_A = +1
     V r = d[first];
@@ -462,15 +462,15 @@ __device__ __forceinline__ V axis_sum(const V* d) {
     }
     return r;
 }
-template <int Q, class V>
-__device__ __forceinline__ void moments_x(const V* d, V& drho, V& jx, V& jy, V& jz) {
+template <int Q, class V, class Pop>
+__device__ __forceinline__ void moments_x(const Pop& d, V& drho, V& jx, V& jy, V& jz) {
     V s = d[0];
 #pragma unroll
     for (int i = 1; i < Q; ++i) s = add_(s, d[i]);
     drho = s;
-    jx = axis_sum<Q, 0>(d);
-    jy = axis_sum<Q, 1>(d);
-    jz = Q == 9 ? V(typename Lane<V>::S(0)) : axis_sum<Q, 2>(d);
+    jx = axis_sum<Q, 0, V>(d);
+    jy = axis_sum<Q, 1, V>(d);
+    jz = Q == 9 ? V(typename Lane<V>::S(0)) : axis_sum<Q, 2, V>(d);
 }
 
 // Zeroth and first moments of deviations d_i = g_i - w_i (Def. moments): drho =
@@ -505,34 +505,37 @@ __device__ __forceinline__ void velocity(C jx, C jy, C jz, C inv_rho, const Phys
     uz = fma_(ph.Fz, h, jz * inv_rho);
 }
 
-// Receiver of each final post-collision value: out(i, d_i) runs as soon as d_i
-// is known, so a kernel can store it at once instead of keeping all q values
-// live to the end (NoSink: the values only stay in d).
-struct NoSink {
-    template <class V>
-    __device__ __forceinline__ void operator()(int, V) const {}
+// The collision reads its input populations through `d` (d[i], i < q: an
+// array, or an object that unpacks stored words on each use) and hands every
+// final post-collision value to a sink, out(i, value), as soon as it is known,
+// so a kernel can store it at once instead of keeping all q values live.
+// WriteBack makes the collision in place on an array.
+template <class V>
+struct WriteBack {
+    V* d;
+    __device__ __forceinline__ void operator()(int i, V v) const { d[i] = v; }
 };
 
 // One opposite pair (I, opp(I)) of the collision: d_I = keep d_I + even + odd,
 // d_opp = keep d_opp + even - odd.
-template <int Q, int I, class V, class Sink>
-__device__ __forceinline__ void relax_pair(V* d, V keep, V even, V odd, Sink& out) {
+template <int Q, int I, class V, class Pop, class Sink>
+__device__ __forceinline__ void relax_pair(const Pop& d, V keep, V even, V odd, Sink& out) {
     constexpr int J = opp<Q>(I);
-    d[I] = add_(fma_(keep, d[I], even), odd);
-    d[J] = sub_(fma_(keep, d[J], even), odd);
-    out(I, d[I]);
-    out(J, d[J]);
+    const V a = add_(fma_(keep, V(d[I]), even), odd);
+    const V b = sub_(fma_(keep, V(d[J]), even), odd);
+    out(I, a);
+    out(J, b);
 }
 
 // As relax_pair for an odd part that is a single product k (c.j): it enters
 // through an fma (k and -k), never as a product added afterwards.
-template <int Q, int I, class V, class Sink>
-__device__ __forceinline__ void relax_pair_prod(V* d, V keep, V even, V k, V nk, V cj, Sink& out) {
+template <int Q, int I, class V, class Pop, class Sink>
+__device__ __forceinline__ void relax_pair_prod(const Pop& d, V keep, V even, V k, V nk, V cj, Sink& out) {
     constexpr int J = opp<Q>(I);
-    d[I] = fma_(k, cj, fma_(keep, d[I], even));
-    d[J] = fma_(nk, cj, fma_(keep, d[J], even));
-    out(I, d[I]);
-    out(J, d[J]);
+    const V a = fma_(k, cj, fma_(keep, V(d[I]), even));
+    const V b = fma_(nk, cj, fma_(keep, V(d[J]), even));
+    out(I, a);
+    out(J, b);
 }
 
 // sum_a c_a w_a x_a over the nonzero components of direction I as an fma chain
@@ -580,9 +583,9 @@ __device__ __forceinline__ void for_pairs(F&& f) {
 // on GB300) but not a scalar one, so no product here is added or subtracted
 // after rounding: products only feed multiplies and fmas. That keeps the paired
 // and the scalar evaluations bit-identical.
-template <int Q, class V, bool SCALED = false, bool FX_ONLY = false, class Sink = NoSink>
-__device__ __forceinline__ void collide(V* d, V varpi, const Phys<typename Lane<V>::S>& ph,
-                                        typename Lane<V>::S s = 1, typename Lane<V>::S inv_s = 1, Sink out = Sink()) {
+template <int Q, class V, bool SCALED, bool FX_ONLY, class Pop, class Sink>
+__device__ __forceinline__ void collide(const Pop& d, V varpi, const Phys<typename Lane<V>::S>& ph,
+                                        typename Lane<V>::S s, typename Lane<V>::S inv_s, Sink out) {
     // FX_ONLY: the caller guarantees F = (Fx, 0, 0); the terms with c.F = 0 drop out.
     // With SCALED the d are s * (f - w) on entry and exit; every term below
     // that adds into d carries the factor s (a power of two: exact).
@@ -609,8 +612,7 @@ __device__ __forceinline__ void collide(V* d, V varpi, const Phys<typename Lane<
     const S guo_s = SCALED ? mul_(ph.guo, s) : ph.guo;
     {  // rest population
         const S w = S(L::w(0));
-        d[0] = fma_(keep, d[0], fma_(V(mul_(ph.omega, w)), A, mul_(V(mul_(guo_s, w)), nuF3)));
-        out(0, d[0]);
+        out(0, fma_(keep, V(d[0]), fma_(V(mul_(ph.omega, w)), A, mul_(V(mul_(guo_s, w)), nuF3))));
     }
     const V kv1 = mul_(V(ph.k1), varpi), kv2 = mul_(V(ph.k2), varpi);
     const S g1 = SCALED ? mul_(ph.g1, s) : ph.g1, g2 = SCALED ? mul_(ph.g2, s) : ph.g2;
@@ -649,10 +651,9 @@ __device__ __forceinline__ void collide(V* d, V varpi, const Phys<typename Lane<
 // so the odd part of omega*M_i + S_i is kk (c.j) + (kk/2 + g)(c.F) with
 // kk = (k - g lam) h: the same fma shape as the shift form (and the same rule:
 // no product is added after rounding).
-template <int Q, class V, bool SCALED = false, class Sink = NoSink>
-__device__ __forceinline__ void collide_drag(V* d, V varpi, const Phys<typename Lane<V>::S>& ph,
-                                             typename Lane<V>::S s = 1, typename Lane<V>::S inv_s = 1,
-                                             Sink out = Sink()) {
+template <int Q, class V, bool SCALED, class Pop, class Sink>
+__device__ __forceinline__ void collide_drag(const Pop& d, V varpi, const Phys<typename Lane<V>::S>& ph,
+                                             typename Lane<V>::S s, typename Lane<V>::S inv_s, Sink out) {
     using L = Lat<Q>;
     using S = typename Lane<V>::S;
     V drho_s, jxs, jys, jzs;
@@ -678,8 +679,7 @@ __device__ __forceinline__ void collide_drag(V* d, V varpi, const Phys<typename 
     const S guo_s = SCALED ? mul_(ph.guo, s) : ph.guo;
     {
         const S w = S(L::w(0));
-        d[0] = fma_(keep, d[0], fma_(V(mul_(ph.omega, w)), A, mul_(V(mul_(guo_s, w)), nuG3)));
-        out(0, d[0]);
+        out(0, fma_(keep, V(d[0]), fma_(V(mul_(ph.omega, w)), A, mul_(V(mul_(guo_s, w)), nuG3))));
     }
     const V kk1 = mul_(fma_(V(-ph.g1), lam, V(ph.k1)), h), kk2 = mul_(fma_(V(-ph.g2), lam, V(ph.k2)), h);
     const S g1 = SCALED ? mul_(ph.g1, s) : ph.g1, g2 = SCALED ? mul_(ph.g2, s) : ph.g2;
@@ -706,10 +706,9 @@ __device__ __forceinline__ void collide_drag(V* d, V varpi, const Phys<typename 
 // v = (vx ux, vy uy, vz uz), a per-axis drag nu/K_a. As collide(), with the
 // odd part k (c.(varpi o j)) + (k/2 c.(varpi o F) + g c.F); the weighted dot
 // products are fma chains.
-template <int Q, class V, bool SCALED = false, class Sink = NoSink>
-__device__ __forceinline__ void collide_aniso(V* d, V wx, V wy, V wz, const Phys<typename Lane<V>::S>& ph,
-                                              typename Lane<V>::S s = 1, typename Lane<V>::S inv_s = 1,
-                                              Sink out = Sink()) {
+template <int Q, class V, bool SCALED, class Pop, class Sink>
+__device__ __forceinline__ void collide_aniso(const Pop& d, V wx, V wy, V wz, const Phys<typename Lane<V>::S>& ph,
+                                              typename Lane<V>::S s, typename Lane<V>::S inv_s, Sink out) {
     using L = Lat<Q>;
     using S = typename Lane<V>::S;
     V drho_s, jxs, jys, jzs;
@@ -732,8 +731,7 @@ __device__ __forceinline__ void collide_aniso(V* d, V wx, V wy, V wz, const Phys
     const S guo_s = SCALED ? mul_(ph.guo, s) : ph.guo;
     {
         const S w = S(L::w(0));
-        d[0] = fma_(keep, d[0], fma_(V(mul_(ph.omega, w)), A, mul_(V(mul_(guo_s, w)), nuF3)));
-        out(0, d[0]);
+        out(0, fma_(keep, V(d[0]), fma_(V(mul_(ph.omega, w)), A, mul_(V(mul_(guo_s, w)), nuF3))));
     }
     const V hFx = V(mul_(S(0.5), ph.Fx)), hFy = V(mul_(S(0.5), ph.Fy)), hFz = V(mul_(S(0.5), ph.Fz));
     const S g1 = SCALED ? mul_(ph.g1, s) : ph.g1, g2 = SCALED ? mul_(ph.g2, s) : ph.g2;

@@ -146,8 +146,8 @@ __device__ __forceinline__ void advance_cell(const DevSlot& sl, int k, int x, in
 #pragma unroll
     for (int i = 0; i < 19; ++i) d[i] = S::load_raw(fin, gather_index<19, false>(g, nb, cell, i, NATURAL));
     const C vp = C(__ldg(sl.varpi + cell));
-    if (FX) collide<19, C, S::scaled, true>(d, vp, ph, C(sl.scale), C(sl.inv_scale));  // the slot's fx_only
-    else collide<19, C, S::scaled, false>(d, vp, ph, C(sl.scale), C(sl.inv_scale));
+    if (FX) collide<19, C, S::scaled, true>(d, vp, ph, C(sl.scale), C(sl.inv_scale), WriteBack<C>{d});  // fx_only
+    else collide<19, C, S::scaled, false>(d, vp, ph, C(sl.scale), C(sl.inv_scale), WriteBack<C>{d});
 #pragma unroll
     for (int i = 0; i < 19; ++i) S::store_raw(fout, i * (int)g.N + cell, d[i]);
 }
@@ -171,16 +171,11 @@ __device__ __forceinline__ void advance_pair(const DevSlot& sl, int k, int x0, i
     const Nbr<int> nb(g, x0, y, z);
     const int xm1 = x0 == 0 ? g.nx - 1 : -1;
     const int xp2 = x0 + 2 >= g.nx ? -x0 : 2;
-    F2 d[19];  // lane 0: cell x0, lane 1: cell x0 + 1
     const float2 vp = __ldg(reinterpret_cast<const float2*>(sl.varpi + cell));
     const Phys<float> ph = sl.ph;
-    {
-        float d0[19], d1[19];
-        if (FX) pair_gather<19, S, LD_WORDS>(fin, cell, nb, xm1, xp2, d0, d1);
-        else pair_gather<19, S, LD_HALVES>(fin, cell, nb, xm1, xp2, d0, d1);
-#pragma unroll
-        for (int i = 0; i < 19; ++i) d[i] = F2(d0[i], d1[i]);
-    }
+    PackedPairs<S, 19> d;  // the loaded words; lane 0: cell x0, lane 1: cell x0 + 1
+    if (FX) pair_gather_words<19, S, LD_WORDS>(fin, cell, nb, xm1, xp2, d.w);
+    else pair_gather_words<19, S, LD_HALVES>(fin, cell, nb, xm1, xp2, d.w);
     const auto store = [&](int i, F2 v) {  // one 32-bit word per direction, stored once final
         const float2 f = v.split();
         *reinterpret_cast<unsigned*>(fout + (i * N + cell)) = P::pack(f.x, f.y);
