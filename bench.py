@@ -47,8 +47,14 @@ FALLBACK_HBM_GBS = 6800.0
 # the bench reports traffic as null instead of a stale figure.
 KERNEL_TRAFFIC_BYTES = {
     # k_step<19, StoreF32, periodic, two-lattice, int, shift-fx>, 256^3: mean of two launches
-    # (1342211840 + 1221328384 and 1342430208 + 1225819136 bytes)
-    ("stream_collide_d3q19_f32_two", 256): {"bytes": 2565894784, "source_hash": "8cf1f08c6b6347f2"},
+    # (1342250752 + 1228698112 and 1342237696 + 1217931008 bytes)
+    ("stream_collide_d3q19_f32_two", 256): {"bytes": 2565558784, "source_hash": "4c3cc9f2e628ed59"},
+    # k_step_pair<19, StoreF16, shift-fx>, 384^3 Boolean sphere matrix: mean of two launches
+    # (2378306304 + 2107552512 and 2378271232 + 2106358016 bytes)
+    ("stream_collide_d3q19_f16_two", 384): {"bytes": 4485244032, "source_hash": "4c3cc9f2e628ed59"},
+    # k_step_pair<19, StoreBF16, shift-fx>, 384^3 Boolean sphere matrix: mean of two launches
+    # (2378304512 + 2109267712 and 2378284032 + 2108000000 bytes)
+    ("stream_collide_d3q19_bf16_two", 384): {"bytes": 4486928128, "source_hash": "4c3cc9f2e628ed59"},
 }
 
 STEP_KERNEL_SOURCES = ("lattice.cuh", "k_step.cuh", "k_step_pair.cuh", "k_step.cu", "k_step_f64.cu",
@@ -330,8 +336,14 @@ def lattice_leg(w, field, storage, pattern, inner, steps, warmup, stream):
     bpl = 2 * q * hb.STORAGE_BYTES[storage] + 4
     peak, kind = measured_hbm_peak()
     achieved = bpl * cells / (kern_ms * 1e-3) / 1e9
+    sname = {v: k for k, v in (("f64", hb.HLBM_F64), ("f32", hb.HLBM_F32), ("f16", hb.HLBM_F16DEV),
+                               ("bf16", hb.HLBM_BF16DEV))}[storage]
+    kname = "stream_collide_d%dq%d_%s_%s" % (3 if q == 19 else 2, q, sname,
+                                             "aa" if pattern == hb.HLBM_AA else "two")
+    traffic, note = kernel_traffic(kname, n)
     return {"glups": cells * inner / (ms_step * 1e-3) / 1e9, "ms_per_step": ms_step, "kernel_ms": kern_ms,
             "bytes_per_lup": bpl, "achieved_GBps": achieved, "frac": achieved / peak, "peak_kind": kind,
+            "kernel": kname, "traffic": traffic, "traffic_note": note,
             "k_app": st["k_app"], "mass_rel_drift": st["mass"] / cells - 1.0}
 
 
@@ -414,6 +426,48 @@ def adjoint_leg(n=128, nsteps=2000, every=45, period=32, ratio=0.3, tau=0.6, F=(
             "grad_abs_max": float(grad.abs().max().item())}
 
 
+def served_vs_fp64(trace, res_b, res_p, field_of, max_edge=64, lu_budget=2.5e10, tau=0.6, F=(1e-6, 0.0, 0.0)):
+    """Velocity error of served results against FP64: each request of edge <= max_edge (smallest
+    first, within lu_budget lattice updates) is re-run with FP64 storage and arithmetic on the
+    same field, from the same rest state, to the step count at which the batched server and the
+    plain FP32 loop each returned it; the error is max|u - u64| / max|u64| at that step (the
+    FP64 policy equals the FP64 oracle to round-off in the parity tests)."""
+    import paper_2310_14746_gb300 as hb
+    by_tag = {rq["id"]: rq for rq in trace}
+    plain = {r["tag"]: r for r in res_p}
+    cand = sorted((r for r in res_b if by_tag[r["tag"]]["edge"] <= max_edge and r["tag"] in plain
+                   and r["u"] is not None and plain[r["tag"]]["u"] is not None),
+                  key=lambda r: by_tag[r["tag"]]["edge"] ** 3 * max(r["steps"], plain[r["tag"]]["steps"]))
+    rows, lu = [], 0.0
+    for r in cand:
+        rq, rp = by_tag[r["tag"]], plain[r["tag"]]
+        n = rq["edge"]
+        cost = float(n) ** 3 * max(r["steps"], rp["steps"])
+        if lu + cost > lu_budget:
+            break
+        lu += cost
+        lat = hb.Lattice(19, n, n, n, hb.HLBM_F64, hb.HLBM_TWO_LATTICE)
+        lat.set_relaxation(tau)
+        lat.set_force(*F)
+        lat.set_porosity(field_of(rq))
+        lat.init_equilibrium()
+        err, done = {}, 0
+        for name, steps, u in sorted((("batched", r["steps"], r["u"]), ("plain_f32", rp["steps"], rp["u"])),
+                                     key=lambda t: t[1]):
+            lat.step(steps - done)
+            done = steps
+            u64 = lat.moments(f64=True)[1]
+            err[name] = float(np.abs(u.astype(np.float64) - u64).max() / np.abs(u64).max())
+        lat.close()
+        rows.append({"edge": n, "steps_batched": r["steps"], "steps_plain": rp["steps"],
+                     "batched": err["batched"], "plain_f32": err["plain_f32"]})
+    if not rows:
+        return None
+    return {"requests": len(rows), "max_batched": max(x["batched"] for x in rows),
+            "max_plain_f32": max(x["plain_f32"] for x in rows), "per_request": rows,
+            "reference": "FP64 storage and arithmetic on the GPU, same field and step count"}
+
+
 def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, world=1, dist=None,
                 capacity_requests=0):
     """Serving stream sample: the first n_requests of the seeded trace (edges up to max_edge).
@@ -458,9 +512,11 @@ def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, 
     kp = {r["tag"]: r["k_app"] for r in res_p}
     kerr = max(abs(kb[k] - kp[k]) / abs(kp[k]) for k in kb if k in kp and kp[k] != 0)
     uerr = None
+    fp64 = None
     if want_u:
         ub = {r["tag"]: r["u"] for r in res_b}
         uerr = max(float(np.abs(ub[r["tag"]] - r["u"]).max() / np.abs(r["u"]).max()) for r in res_p)
+        fp64 = served_vs_fp64(trace, res_b, res_p, field_of)
     cells_of = {rq["id"]: rq["edge"] ** 3 for rq in trace}
     lu_all = sum(r["steps"] * cells_of[r["tag"]] for r in res_b)
     lu_low = sum(r["steps_low"] * cells_of[r["tag"]] for r in res_b)
@@ -501,10 +557,59 @@ def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, 
                       "converged": sum(r["status"] == 0 for r in res_p)},
         "k_app_rel_diff_f16_batched_vs_f32_plain": kerr,
         "velocity_rel_diff_batched_vs_f32_plain": uerr,
+        "velocity_rel_err_vs_fp64": fp64,
         "lattice_update_share_16bit": lu_low / max(lu_all, 1),
         "per_request": per_request,
         "steps": {"min": int(min(r["steps"] for r in res_b)), "max": int(max(r["steps"] for r in res_b))},
     }
+
+
+def serving_class_leg(edge, count, storage_name, rounds=20, warm_rounds=3, check_every=100, period=32, ratio=0.3):
+    """Throughput of one kernel class of the batched server: `count` identical slots of edge `edge`
+    (regular sphere matrix) in `storage_name`, all in every round (processor sharing), never retired
+    or widened (a tolerance of 1e-300, no refinement). Each round is check_every batched time steps (one graph
+    replay) plus the per-slot FP64 check, timed on the host around hlbm_server_pump (which
+    synchronises). Returns GLUPS and the fraction of the measured copy bandwidth at the storage's
+    algorithmic bytes per lattice update."""
+    import paper_2310_14746_gb300 as hb
+    from paper_2310_14746_gb300 import inputs
+    from paper_2310_14746_gb300 import serving as sv
+    storage = {"f32": hb.HLBM_F32, "f16": hb.HLBM_F16DEV, "bf16": hb.HLBM_BF16DEV}[storage_name]
+    field = inputs.regular_sphere_field(edge, period=min(period, edge), radius_ratio=ratio)
+    srv = sv.Server(96 << 30, storage, check_every, refine=False, backfill=1e6)
+    for k in range(count):
+        srv.submit(field, tol=1e-300, max_steps=10 ** 9, tag=k)
+    for _ in range(warm_rounds):
+        srv.pump()
+    t0 = time.perf_counter()
+    for _ in range(rounds):
+        a, _w = srv.pump()
+    dt = time.perf_counter() - t0
+    srv.close()
+    if a != count:
+        raise RuntimeError("serving class: %d of %d slots live" % (a, count))
+    lups = float(count) * edge ** 3 * check_every * rounds
+    bpl = 2 * 19 * hb.STORAGE_BYTES[storage] + 4
+    peak, kind = measured_hbm_peak()
+    return {"edge": edge, "slots": count, "storage": storage_name, "rounds": rounds, "check_every": check_every,
+            "seconds": dt, "glups": lups / dt / 1e9, "bytes_per_lup": bpl,
+            "achieved_GBps": bpl * lups / dt / 1e9, "frac": bpl * lups / dt / 1e9 / peak, "peak_kind": kind,
+            "slot_bytes": edge ** 3 * 19 * hb.STORAGE_BYTES[storage] * 2}
+
+
+def run_serving_class(args, local_rank):
+    """--serving-class EDGE:COUNT:STORAGE[,...]: one JSON line with each class's throughput."""
+    import torch
+    from paper_2310_14746_gb300 import build
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local_rank)
+    build.build()
+    out = []
+    for spec in args.serving_class.split(","):
+        e, c, s = spec.split(":")
+        out.append(serving_class_leg(int(e), int(c), s, rounds=args.steps, warm_rounds=max(1, args.warmup)))
+    print(json.dumps({"metric": METRIC, "impl": "ours", "mode": "serving-class", "classes": out}), flush=True)
 
 
 def run_serving_only(args, rank, world, local_rank):
@@ -682,6 +787,10 @@ def main():
                     help="measure the batched capacity on the first K requests only (0: all of them)")
     ap.add_argument("--serving-only", action="store_true",
                     help="run only the serving leg (long traces) and print its JSON object")
+    ap.add_argument("--serving-class", default="",
+                    help="EDGE:COUNT:STORAGE[,...] (storage f32|f16|bf16): time these batched-server kernel "
+                         "classes (COUNT identical slots each, --steps rounds after --warmup) and print their "
+                         "throughput only")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient leg")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the AA, reduced-precision and adjoint legs (the main line only)")
@@ -695,6 +804,8 @@ def main():
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w, rank)
+    elif args.serving_class:
+        run_serving_class(args, local_rank)
     elif args.serving_only:
         run_serving_only(args, rank, world, local_rank)
     else:
