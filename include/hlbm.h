@@ -117,6 +117,17 @@ int hlbm_create(hlbm_t** out, int velset, int nx, int ny, int nz, int storage, i
 /* Free the handle and its device memory (after draining its stream). NULL is a no-op. */
 void hlbm_destroy(hlbm_t* h);
 
+/* Temporary device memory of the calls that need it (the checkpoints of
+ * hlbm_adjoint_flux_grad, staging buffers of host-array I/O) comes, ordered on
+ * the handle's stream, from a memory pool private to the handle, which keeps
+ * the memory it has mapped for the next call instead of handing it back at
+ * each synchronisation (re-mapping the 14.5 GB of checkpoints of a 128^3 x
+ * 2000-step gradient took about 15 % of the call). This call waits for the
+ * handle's stream and returns the pool's unused memory to the device; the
+ * next call that needs scratch maps it again. Not a paper operation (memory
+ * management of this library). */
+int hlbm_release_scratch(hlbm_t* h);
+
 /* Replace the stream later work is enqueued on. */
 int hlbm_set_stream(hlbm_t* h, void* cuda_stream);
 
@@ -127,9 +138,13 @@ int hlbm_set_stream(hlbm_t* h, void* cuda_stream);
 int hlbm_set_relaxation(hlbm_t* h, double tau);
 
 /* Per-cell porosity control varpi (eq. "d definition"), nx*ny*nz FP32 values,
- * x-fastest; copied. Every value must lie in [0, 1] (NaN rejected); a host
- * array is validated before the copy, a device array by a check kernel
- * (synchronises). varpi = 1 is plain BGK, varpi = 0 a solid cell. */
+ * x-fastest; copied. Every value must lie in [0, 1] (NaN rejected), checked
+ * by a kernel before the values replace the field: a host array is first
+ * copied to a temporary device buffer (or, when that buffer cannot be
+ * allocated, checked on the host and copied straight into the field). On
+ * HLBM_ERR_INVALID_ARG the field is unchanged. Synchronises; the caller's
+ * array may be reused when the call returns. varpi = 1 is plain BGK,
+ * varpi = 0 a solid cell. */
 int hlbm_set_porosity(hlbm_t* h, const float* varpi, int on_device);
 
 /* Resolved obstacles: nx*ny*nz bytes, nonzero = solid cell (copied; host or

@@ -116,6 +116,7 @@ _d = ctypes.c_double
 SIGNATURES = {
     "hlbm_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _i, _i, _vp]),
     "hlbm_destroy": (None, [_vp]),
+    "hlbm_release_scratch": (_i, [_vp]),
     "hlbm_set_stream": (_i, [_vp, _vp]),
     "hlbm_set_relaxation": (_i, [_vp, _d]),
     "hlbm_set_porosity": (_i, [_vp, _vp, _i]),
@@ -220,6 +221,10 @@ def hlbm_create(velset, nx, ny, nz, storage=HLBM_F32, pattern=HLBM_TWO_LATTICE, 
 
 def hlbm_destroy(h):
     _lib().hlbm_destroy(h)
+
+
+def hlbm_release_scratch(h):
+    _check(_lib().hlbm_release_scratch(h), "hlbm_release_scratch")
 
 
 def hlbm_set_stream(h, stream):
@@ -468,6 +473,10 @@ class Lattice:
         if self.h:
             hlbm_destroy(self.h)
             self.h = None
+
+    def release_scratch(self):
+        """Return the handle's cached scratch memory (hlbm_release_scratch)."""
+        hlbm_release_scratch(self.h)
 
     def __del__(self):
         try:

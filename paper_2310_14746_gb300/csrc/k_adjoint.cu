@@ -28,11 +28,12 @@ static Geometry geom(const LaunchCtx& c) {
     return Geometry{c.nx, c.ny, c.nz, c.wall[0], c.wall[1], c.wall[2], (size_t)c.nx * c.ny * c.nz};
 }
 
-// I: index type (int while every index of the [q][cells] arrays fits). Three
-// blocks of 256 per SM (80 registers): the kernel moves 240 B per cell and
-// needs resident warps to keep that many loads in flight.
+// I: index type (int while every index of the [q][cells] arrays fits). Four
+// blocks of 256 per SM (64 registers, no spills): the kernel moves 240 B per
+// cell and needs resident warps to keep that many loads in flight (five blocks
+// would spill).
 template <int Q, class S, bool WALLS, class I>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
 k_adjoint_step(const typename S::T* __restrict__ fn, const float* __restrict__ lam_in, float* __restrict__ lam_out,
                const float* __restrict__ varpi, float* __restrict__ grad, Geometry g, Phys<typename S::C> ph,
                typename S::C inv_s) {

@@ -259,10 +259,47 @@ k_read_state(const typename S::T* f, int lay, Geometry g, typename S::C inv_s, d
             L::w(i) + (double)S::load(f, natural_index<Q, WALLS>(g, nb, cell, i, lay), inv_s);
 }
 
+// The same state as k_write_state with uniform = 1 (every cell holds fnat[i]),
+// for kFillZ consecutive z planes per thread: the deviation of each direction
+// is formed once per thread (in double, as k_write_state forms it, so the bits
+// are the same), and the per-cell work is only the index and the store. GB300's
+// FP64 rate is a small fraction of its FP32 rate, and the per-cell double
+// subtract and conversion had limited the initial write to about 1.2 TB/s.
+constexpr int kFillZ = 8;
+
+template <int Q, class S, bool WALLS>
+__global__ void __launch_bounds__(256)
+k_fill_state(const double* fnat, int lay, Geometry g, typename S::C s, typename S::T* f, const unsigned* links) {
+    using C = typename S::C;
+    using L = Lat<Q>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= g.nx || y >= g.ny) return;
+    C v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] = C(fnat[i] - L::w(i));
+    const int z0 = blockIdx.z * kFillZ;
+    const int z1 = z0 + kFillZ < g.nz ? z0 + kFillZ : g.nz;
+    for (int z = z0; z < z1; ++z) {
+        const long long cell = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
+        const unsigned lm = links ? links[cell] : 0u;
+        if (lm & kSolidBit) continue;
+        const Nbr<long long> nb(g, x, y, z, lm);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) S::store(f, natural_index<Q, WALLS>(g, nb, cell, i, lay), v[i], s);
+    }
+}
+
 template <int Q, class S, bool WALLS>
 static cudaError_t write_impl(const LaunchCtx& c, int lay, const double* fnat, int uniform, void* f) {
     using C = typename S::C;
     const dim3 blk = block_for(c.nx);
+    if (uniform) {
+        const dim3 grd((c.nx + blk.x - 1) / blk.x, (c.ny + blk.y - 1) / blk.y, (c.nz + kFillZ - 1) / kFillZ);
+        k_fill_state<Q, S, WALLS><<<grd, blk, 0, c.stream>>>(fnat, lay, geom(c), C(c.scale),
+                                                             static_cast<typename S::T*>(f), c.links);
+        return cudaGetLastError();
+    }
     const dim3 grd((c.nx + blk.x - 1) / blk.x, (c.ny + blk.y - 1) / blk.y, c.nz);
     k_write_state<Q, S, WALLS><<<grd, blk, 0, c.stream>>>(fnat, uniform, lay, geom(c), C(c.scale),
                                                           static_cast<typename S::T*>(f), c.links);

@@ -294,6 +294,64 @@ def test_invalid_inputs_rejected():
     lat.close()
 
 
+@pytest.mark.parametrize("on_device", [False, True])
+def test_rejected_porosity_leaves_field_unchanged(on_device):
+    """A rejected field (one value out of [0, 1]) must not replace the accepted one: the
+    lattice then steps bit for bit like a lattice that only ever saw the accepted field."""
+    import torch
+    shape = (6, 8, 10)
+    good = inputs.random_porosity(shape, 11)
+    bad = inputs.random_porosity(shape, 12)
+    bad[3, 4, 5] = 1.25
+    ref = make_lattice(19, shape)
+    ref.set_porosity(good)
+    ref.init_equilibrium()
+    lat = make_lattice(19, shape)
+    lat.set_porosity(good)
+    with pytest.raises(hb.HlbmError) as e:
+        lat.set_porosity(torch.from_numpy(bad).cuda() if on_device else bad)
+    assert e.value.status == hb.HLBM_ERR_INVALID_ARG
+    lat.init_equilibrium()
+    ref.step(24)
+    lat.step(24)
+    np.testing.assert_array_equal(lat.get_populations(), ref.get_populations())
+    ref.close()
+    lat.close()
+
+
+@pytest.mark.parametrize("storage,tol", [(hb.HLBM_F64, 1e-15), (hb.HLBM_F32, 1e-7), (hb.HLBM_F16DEV, 1e-4),
+                                         (hb.HLBM_BF16DEV, 1e-3)])
+@pytest.mark.parametrize("pattern", [hb.HLBM_TWO_LATTICE, hb.HLBM_AA])
+@pytest.mark.parametrize("walls", [False, True])
+def test_uniform_init_state(storage, tol, pattern, walls, oracle):
+    """init_equilibrium (the uniform fill kernel, several z planes per thread; a ragged last
+    group of planes) stores the equilibrium of (rho0, u0) in every cell and direction: read back,
+    it equals the oracle's equilibrium within the storage's rounding. For the 32- and 16-bit
+    policies the read-back state, written again with set_populations, steps bit for bit like
+    the filled one (same layout handling in both write kernels)."""
+    nz, ny, nx = 13, 6, 10
+    rho0, u0 = 1.01, (0.02, -0.01, 0.015)
+    a = hb.Lattice(19, nx, ny, nz, storage, pattern)
+    b = hb.Lattice(19, nx, ny, nz, storage, pattern)
+    for lat in (a, b):
+        lat.set_relaxation(0.7)
+        if walls:
+            lat.set_boundary(1, hb.HLBM_HALFWAY_BOUNCE_BACK)
+    a.init_equilibrium(rho0, u0)
+    fa = a.get_populations()
+    ref = oracle.equilibrium_state(19, (nz, ny, nx), rho0, u0)
+    np.testing.assert_allclose(fa, ref, rtol=0, atol=tol)
+    if storage != hb.HLBM_F64:
+        b.set_populations(fa)
+        vp = inputs.random_porosity((nz, ny, nx), 5)
+        for lat in (a, b):
+            lat.set_porosity(vp)
+            lat.step(3)
+        np.testing.assert_array_equal(a.get_populations(), b.get_populations())
+    a.close()
+    b.close()
+
+
 def test_device_buffers_and_streams():
     """Porosity from a CUDA tensor, moments into CUDA tensors, on a side stream."""
     import torch

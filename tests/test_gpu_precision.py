@@ -54,3 +54,55 @@ def test_reduced_precision_error_96(reference, storage, bound, pattern):
     assert eu <= bound
     assert ek <= bound
     assert abs(drift) < 1e-3
+
+
+@pytest.mark.parametrize("storage,tol1,tol9", [(hb.HLBM_F16DEV, 1e-4, 5e-4), (hb.HLBM_BF16DEV, 6e-4, 3e-3)])
+def test_full_size_384_sampled_cells(oracle, storage, tol1, tol9):
+    """The reduced-precision workload at full size, in the launch configuration the bench times
+    (384^3, the random Boolean sphere matrix, F along x: the paired two-cells-per-thread kernel,
+    a direct launch and then one 8-step graph replay), from a random state near equilibrium,
+    f_i = w_i (1 + 0.1 U(-1, 1)). 32 sampled cells are compared with the oracle run on their
+    dependency cone (radius 10 around the cell, periodic wrap errors reach 1 cell per step).
+    Tolerances are the 16-bit storage rounding: deviations |f - w| <= 0.1 w_i are stored with an
+    11-bit (FP16, scaled by 2^12: ulp <= 2^-15 = 3.1e-5 for the rest population, at most 3.8e-6
+    for the others) or 8-bit (BF16: ulp <= 2^-12 = 2.4e-4, and 3.1e-5) significand. The initial
+    state and every step add at most half an ulp per population; through the density sum and the
+    equilibrium (omega = 1/0.6) one step's worst case is about 5e-5 (FP16) and 3.7e-4 (BF16), so
+    the bounds are 1e-4 / 6e-4 after 1 step and 5e-4 / 3e-3 after 9. A population taken from the
+    wrong neighbour or direction differs by about 0.1 w_i >= 2.8e-3 on this state, far above the
+    1-step bounds."""
+    import torch
+    n, rad, q = 384, 10, 19
+    tau, F = 0.6, (1e-6, 0.0, 0.0)
+    field, _ = inputs.random_sphere_field(n, SEED)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    rng = np.random.default_rng(SEED + 100)
+    f0 = rng.random((q, n, n, n))
+    f0 *= 0.2
+    f0 += 0.9
+    f0 *= w[:, None, None, None]
+    cells = [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(32)]
+    subs = []
+    for z, y, x in cells:
+        idx = [np.arange(c - rad, c + rad + 1) % n for c in (z, y, x)]
+        subs.append((f0[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]].copy(),
+                     field[idx[0]][:, idx[1]][:, :, idx[2]].astype(np.float64)))
+    lat = make_lattice(19, (n, n, n), storage, hb.HLBM_TWO_LATTICE, tau, F, (0, 0, 0), varpi=field, f0=f0)
+    del f0
+    out = torch.empty((q, n, n, n), dtype=torch.float64, device="cuda")
+    zi = torch.tensor([c[0] for c in cells], device="cuda")
+    yi = torch.tensor([c[1] for c in cells], device="cuda")
+    xi = torch.tensor([c[2] for c in cells], device="cuda")
+    done = 0
+    for steps, tol in ((1, tol1), (9, tol9)):
+        lat.step(steps - done)  # 1 direct launch, then one graph replay of 8
+        done = steps
+        hb.hlbm_get_populations(lat.h, out)
+        torch.cuda.synchronize()
+        got = out[:, zi, yi, xi].cpu().numpy()
+        for k, (sub, svp) in enumerate(subs):
+            ref = oracle.run(sub, svp, tau, F, (0, 0, 0), steps)
+            np.testing.assert_allclose(got[:, k], ref[:, rad, rad, rad], rtol=0, atol=tol)
+    lat.close()
+    del out
+    torch.cuda.empty_cache()
