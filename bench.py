@@ -42,30 +42,38 @@ METRIC = "D3Q19 HBGK MLUPS & % HBM roofline; p50/p99 solve latency, batched vs p
 FALLBACK_HBM_GBS = 6800.0
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from the
-# ncu capture summarised under profiles/. Each entry records the hash of the step-kernel
-# sources it was captured from (kernel_source_hash()); when the sources have changed since,
-# the bench reports traffic as null instead of a stale figure.
+# ncu capture summarised under profiles/. Each entry records the hash of the sources of that
+# kernel (kernel_source_hash(kernel)) it was captured from; when those sources have changed
+# since, the bench reports traffic as null instead of a stale figure.
 KERNEL_TRAFFIC_BYTES = {
     # k_step<19, StoreF32, periodic, two-lattice, int, shift-fx>, 256^3: mean of two launches
     # (1342250752 + 1228698112 and 1342237696 + 1217931008 bytes)
-    ("stream_collide_d3q19_f32_two", 256): {"bytes": 2565558784, "source_hash": "4c3cc9f2e628ed59"},
+    ("stream_collide_d3q19_f32_two", 256): {"bytes": 2565558784, "source_hash": "76d4a47919d1105a"},
     # k_step_pair<19, StoreF16, shift-fx>, 384^3 Boolean sphere matrix: mean of two launches
     # (2378306304 + 2107552512 and 2378271232 + 2106358016 bytes)
-    ("stream_collide_d3q19_f16_two", 384): {"bytes": 4485244032, "source_hash": "4c3cc9f2e628ed59"},
+    ("stream_collide_d3q19_f16_two", 384): {"bytes": 4485244032, "source_hash": "50d4b8b26d87e80e"},
     # k_step_pair<19, StoreBF16, shift-fx>, 384^3 Boolean sphere matrix: mean of two launches
     # (2378304512 + 2109267712 and 2378284032 + 2108000000 bytes)
-    ("stream_collide_d3q19_bf16_two", 384): {"bytes": 4486928128, "source_hash": "4c3cc9f2e628ed59"},
+    ("stream_collide_d3q19_bf16_two", 384): {"bytes": 4486928128, "source_hash": "33b18be91f62e7c5"},
 }
 
-STEP_KERNEL_SOURCES = ("lattice.cuh", "k_step.cuh", "k_step_pair.cuh", "k_step.cu", "k_step_f64.cu",
-                       "k_step_f32.cu", "k_step_f16.cu", "k_step_bf16.cu")
+# the sources each step kernel is compiled from (csrc/)
+_COMMON_SOURCES = ("lattice.cuh", "internal.h", "k_step.cuh", "k_step.cu")
+KERNEL_SOURCES = {
+    "f64": _COMMON_SOURCES + ("k_step_f64.cu",),
+    "f32": _COMMON_SOURCES + ("k_step_f32.cu",),
+    "f16": _COMMON_SOURCES + ("k_step_pair.cuh", "k_step_f16.cu"),
+    "bf16": _COMMON_SOURCES + ("k_step_pair.cuh", "k_step_bf16.cu"),
+}
 
 
-def kernel_source_hash():
-    """sha256 (first 16 hex digits) over the sources of the step kernels."""
+def kernel_source_hash(kname):
+    """sha256 (first 16 hex digits) over the sources of the step kernel `kname`
+    (stream_collide_d3q19_<storage>_<pattern>)."""
     import hashlib
+    storage = kname.split("_")[3]
     h = hashlib.sha256()
-    for name in STEP_KERNEL_SOURCES:
+    for name in KERNEL_SOURCES[storage]:
         with open(os.path.join(ROOT, "paper_2310_14746_gb300", "csrc", name), "rb") as fh:
             h.update(name.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
@@ -76,7 +84,7 @@ def kernel_traffic(kname, n):
     e = KERNEL_TRAFFIC_BYTES.get((kname, n))
     if e is None:
         return None, "not captured"
-    if e["source_hash"] != kernel_source_hash():
+    if e["source_hash"] != kernel_source_hash(kname):
         return None, "stale: kernel sources changed since the capture"
     return e["bytes"], "ncu capture of these sources"
 
@@ -790,7 +798,7 @@ def run_gpu(args, w, rank, world, local_rank):
                        "l2": "inputs larger than L2 (%.2f GB streamed per time step)" % (bytes_per_lup * cells / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
-                         "kernel_source_hash": kernel_source_hash(), "peak_kind": peak_kind,
+                         "kernel_source_hash": kernel_source_hash(kname), "peak_kind": peak_kind,
                          "kernel": kname, "kernel_ms": kern_ms, "bytes_per_lup": bytes_per_lup},
             "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
