@@ -49,12 +49,15 @@ KERNEL_TRAFFIC_BYTES = {
     # k_step<19, StoreF32, periodic, two-lattice, int, shift-fx>, 256^3: mean of two launches
     # (1342250752 + 1228698112 and 1342237696 + 1217931008 bytes)
     ("stream_collide_d3q19_f32_two", 256): {"bytes": 2565558784, "source_hash": "76d4a47919d1105a"},
-    # k_step_pair<19, StoreF16, shift-fx>, 384^3 Boolean sphere matrix: mean of two launches
-    # (2378306304 + 2107552512 and 2378271232 + 2106358016 bytes)
-    ("stream_collide_d3q19_f16_two", 384): {"bytes": 4485244032, "source_hash": "50d4b8b26d87e80e"},
-    # k_step_pair<19, StoreBF16, shift-fx>, 384^3 Boolean sphere matrix: mean of two launches
-    # (2378304512 + 2109267712 and 2378284032 + 2108000000 bytes)
-    ("stream_collide_d3q19_bf16_two", 384): {"bytes": 4486928128, "source_hash": "33b18be91f62e7c5"},
+    # k_step_pair<19, StoreF16, shift-fx, two-lattice>, 384^3 Boolean sphere matrix: mean of two launches
+    # (2378683648 + 2107668736 and 2378212864 + 2106361088 bytes)
+    ("stream_collide_d3q19_f16_two", 384): {"bytes": 4485463168, "source_hash": "4c5af8f94e7e5453"},
+    # k_step_pair<19, StoreBF16, shift-fx, two-lattice>, 384^3 Boolean sphere matrix: mean of two launches
+    # (2378648064 + 2109742336 and 2378214912 + 2107992064 bytes)
+    ("stream_collide_d3q19_bf16_two", 384): {"bytes": 4487298688, "source_hash": "7aa28bbe2bf10de0"},
+    # k_step_pair<19, StoreF16, shift-fx, AA even / AA odd>, 384^3 Boolean sphere matrix: mean of the
+    # even (2378228736 + 2098037760) and odd (2378235392 + 2152788992 bytes) launch of one capture
+    ("stream_collide_d3q19_f16_aa", 384): {"bytes": 4503645440, "source_hash": "4c5af8f94e7e5453"},
 }
 
 # the sources each step kernel is compiled from (csrc/)
@@ -280,6 +283,15 @@ def oracle_reference_96(w, field96, steps):
             "sample": "%d FP64 oracle time steps of the 96^3 resampled field" % steps}, u, st["k_app"]
 
 
+def workload_config(w, check_every, world):
+    """The `config` object of the bench line (the same for both arms)."""
+    bpl = 2 * w["q"] * {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[w["storage"]] + 4
+    cells = w["n"] ** 3
+    return {"workload": w["desc"], "cells": cells, "time_steps_per_step": check_every, "check_every": check_every,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2 (%.2f GB streamed per time step)" % (bpl * cells / 1e9)}
+
+
 def run_reference(args, w, rank):
     if rank != 0:
         return
@@ -296,10 +308,11 @@ def run_reference(args, w, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / total_steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": w["desc"], "cells": w["n"] ** 3,
-                                        "step": "one oracle time step"},
+        "data": "synthetic", "config": workload_config(w, args.check_every, args.gpus),
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                         "sample": "%d FP64 oracle time steps of the full %d^3 lattice" % (steps, w["n"])},
+                         "sample": "%d FP64 oracle time steps of the full %d^3 lattice (each timed step of this "
+                                   "arm is one oracle time step, a bounded sample of the workload)"
+                                   % (steps, w["n"])},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -599,21 +612,34 @@ def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, 
     }
 
 
-def serving_class_leg(edge, count, storage_name, rounds=20, warm_rounds=3, check_every=100, period=32, ratio=0.3):
-    """Throughput of one kernel class of the batched server: `count` identical slots of edge `edge`
-    (regular sphere matrix) in `storage_name`, all in every round (processor sharing), never retired
-    or widened (a tolerance of 1e-300, no refinement). Each round is check_every batched time steps (one graph
+def serving_class_leg(groups, rounds=20, warm_rounds=3, check_every=100, period=32, ratio=0.3):
+    """Throughput of kernel classes of the batched server: for each (edge, count, storage) of
+    `groups`, `count` identical slots of edge `edge` (regular sphere matrix) in `storage`, all of
+    them in one server and in every round (processor sharing), never retired or widened (a
+    tolerance of 1e-300, no refinement). Each round is check_every batched time steps (one graph
     replay) plus the per-slot FP64 check, timed on the host around hlbm_server_pump (which
-    synchronises). Returns GLUPS and the fraction of the measured copy bandwidth at the storage's
+    synchronises). Returns GLUPS and the fraction of the measured copy bandwidth at the storages'
     algorithmic bytes per lattice update."""
     import paper_2310_14746_gb300 as hb
     from paper_2310_14746_gb300 import inputs
     from paper_2310_14746_gb300 import serving as sv
-    storage = {"f32": hb.HLBM_F32, "f16": hb.HLBM_F16DEV, "bf16": hb.HLBM_BF16DEV}[storage_name]
-    field = inputs.regular_sphere_field(edge, period=min(period, edge), radius_ratio=ratio)
-    srv = sv.Server(96 << 30, storage, check_every, refine=False, backfill=1e6)
-    for k in range(count):
-        srv.submit(field, tol=1e-300, max_steps=10 ** 9, tag=k)
+    kinds = {"f32": hb.HLBM_F32, "f16": hb.HLBM_F16DEV, "bf16": hb.HLBM_BF16DEV}
+    srv = sv.Server(96 << 30, kinds[groups[0][2]], check_every, refine=False, backfill=1e6)
+    total, lups, byts, tag = 0, 0.0, 0.0, 0
+    for edge, count, storage_name in groups:
+        storage = kinds[storage_name]
+        # a request's storage is the server's (it starts every slot in that storage); a group in
+        # another storage needs its own server, so mixed specs keep one storage
+        if storage != kinds[groups[0][2]]:
+            raise SystemExit("--serving-class: the groups of one spec share a storage")
+        field = inputs.regular_sphere_field(edge, period=min(period, edge), radius_ratio=ratio)
+        for _ in range(count):
+            srv.submit(field, tol=1e-300, max_steps=10 ** 9, tag=tag)
+            tag += 1
+        total += count
+        cells = float(count) * edge ** 3
+        lups += cells * check_every * rounds
+        byts += cells * check_every * rounds * (2 * 19 * hb.STORAGE_BYTES[storage] + 4)
     for _ in range(warm_rounds):
         srv.pump()
     t0 = time.perf_counter()
@@ -621,15 +647,12 @@ def serving_class_leg(edge, count, storage_name, rounds=20, warm_rounds=3, check
         a, _w = srv.pump()
     dt = time.perf_counter() - t0
     srv.close()
-    if a != count:
-        raise RuntimeError("serving class: %d of %d slots live" % (a, count))
-    lups = float(count) * edge ** 3 * check_every * rounds
-    bpl = 2 * 19 * hb.STORAGE_BYTES[storage] + 4
+    if a != total:
+        raise RuntimeError("serving class: %d of %d slots live" % (a, total))
     peak, kind = measured_hbm_peak()
-    return {"edge": edge, "slots": count, "storage": storage_name, "rounds": rounds, "check_every": check_every,
-            "seconds": dt, "glups": lups / dt / 1e9, "bytes_per_lup": bpl,
-            "achieved_GBps": bpl * lups / dt / 1e9, "frac": bpl * lups / dt / 1e9 / peak, "peak_kind": kind,
-            "slot_bytes": edge ** 3 * 19 * hb.STORAGE_BYTES[storage] * 2}
+    return {"groups": [{"edge": e, "slots": c, "storage": st} for e, c, st in groups], "rounds": rounds,
+            "check_every": check_every, "seconds": dt, "glups": lups / dt / 1e9,
+            "achieved_GBps": byts / dt / 1e9, "frac": byts / dt / 1e9 / peak, "peak_kind": kind}
 
 
 def run_adjoint_only(args, local_rank):
@@ -654,8 +677,8 @@ def run_serving_class(args, local_rank):
     build.build()
     out = []
     for spec in args.serving_class.split(","):
-        e, c, s = spec.split(":")
-        out.append(serving_class_leg(int(e), int(c), s, rounds=args.steps, warm_rounds=max(1, args.warmup)))
+        groups = [(int(e), int(c), st) for e, c, st in (g.split(":") for g in spec.split("+"))]
+        out.append(serving_class_leg(groups, rounds=args.steps, warm_rounds=max(1, args.warmup)))
     print(json.dumps({"metric": METRIC, "impl": "ours", "mode": "serving-class", "classes": out}), flush=True)
 
 
@@ -793,9 +816,7 @@ def run_gpu(args, w, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": w["storage"], "data": "synthetic",
-            "config": {"workload": w["desc"], "cells": cells, "time_steps_per_step": inner,
-                       "check_every": inner, "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (%.2f GB streamed per time step)" % (bytes_per_lup * cells / 1e9)},
+            "config": workload_config(w, inner, world),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
                          "kernel_source_hash": kernel_source_hash(kname), "peak_kind": peak_kind,
@@ -835,9 +856,9 @@ def main():
     ap.add_argument("--serving-only", action="store_true",
                     help="run only the serving leg (long traces) and print its JSON object")
     ap.add_argument("--serving-class", default="",
-                    help="EDGE:COUNT:STORAGE[,...] (storage f32|f16|bf16): time these batched-server kernel "
-                         "classes (COUNT identical slots each, --steps rounds after --warmup) and print their "
-                         "throughput only")
+                    help="EDGE:COUNT:STORAGE[+EDGE:COUNT:STORAGE...][,...] (storage f32|f16|bf16): time these "
+                         "batched-server slot sets (COUNT identical slots per group, the groups of one spec in one "
+                         "server, --steps rounds after --warmup) and print their throughput only")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint-gradient leg (--adjoint-n, --adjoint-steps) and print it")
     ap.add_argument("--adjoint-n", type=int, default=128)

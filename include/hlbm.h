@@ -122,7 +122,7 @@ void hlbm_destroy(hlbm_t* h);
  * the handle's stream, from a memory pool private to the handle, which keeps
  * the memory it has mapped for the next call instead of handing it back at
  * each synchronisation (re-mapping the 14.5 GB of checkpoints of a 128^3 x
- * 2000-step gradient took about 15 % of the call). This call waits for the
+ * 2000-step gradient took about 7 % of the call). This call waits for the
  * handle's stream and returns the pool's unused memory to the device; the
  * next call that needs scratch maps it again. Not a paper operation (memory
  * management of this library). */
@@ -351,8 +351,9 @@ typedef struct {
  * must then meet its tolerance in FP32. Scheduling: every round the oldest
  * live request advances check_every steps, and younger ones join it in age
  * order within a cell budget (hlbm_server_set_priority). Slots of at least
- * 2^19 cells run the single-lattice step kernels inside the round's graph;
- * smaller ones share a batched kernel; both give the same bits. */
+ * 2^18 cells (64^3) run the single-lattice step kernels inside the round's
+ * graph, in parallel branches of it; smaller ones share a batched kernel; both
+ * give the same bits. */
 int hlbm_server_create(hlbm_server_t** out, size_t mem_budget, int storage, int check_every,
                        void* cuda_stream);
 /* Turn refinement on or off and set its floor coefficient (>= 0). With it off,

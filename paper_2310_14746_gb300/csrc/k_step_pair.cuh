@@ -1,5 +1,6 @@
 // Two-cells-per-thread stream-and-collide for 16-bit storage (FP16 and BF16
-// deviations), periodic two-lattice lattices with an even nx.
+// deviations), periodic lattices with an even nx: two-lattice pull streaming
+// and both steps of the in-place AA pattern.
 //
 // The per-cell kernel spends most of its issue slots on work that does not
 // scale with the bytes it moves: 16-bit loads and stores, one conversion per
@@ -125,7 +126,17 @@ __device__ __forceinline__ void pair_gather(const Planes<const typename S::T, Q>
 
 // The same gather keeping each direction's pair as one 32-bit word (lane 0 in
 // the low half): 19 registers instead of 38, unpacked exactly where used.
-template <int Q, class S, int LD>
+// INPLACE (the odd AA step, whose source is also its destination): plain
+// coherent loads instead of the read-only path, and only 16-bit loads on the
+// x-shifted directions, so that a thread reads no population another thread
+// of the launch writes.
+template <class V, bool INPLACE, class P>
+__device__ __forceinline__ V ld_pop(const P* p) {
+    if constexpr (INPLACE) return *reinterpret_cast<const V*>(p);  // may alias this launch's stores
+    else return __ldg(reinterpret_cast<const V*>(p));
+}
+
+template <int Q, class S, int LD, bool INPLACE = false>
 __device__ __forceinline__ void pair_gather_words(const Planes<const typename S::T, Q>& fin, int cell,
                                                   const Nbr<int>& nb, int xm1, int xp2, unsigned* w) {
     using L = Lat<Q>;
@@ -139,15 +150,16 @@ __device__ __forceinline__ void pair_gather_words(const Planes<const typename S:
         if (L::cz(i) < 0) o += nb.ozp;
         const T* row = fin.p[i] + (cell + o);
         if (L::cx(i) == 0) {
-            w[i] = __ldg(reinterpret_cast<const unsigned*>(row));
-        } else if (LD == LD_WORDS) {
+            w[i] = ld_pop<unsigned, INPLACE>(row);
+        } else if (LD == LD_WORDS && !INPLACE) {
             const unsigned b = __ldg(reinterpret_cast<const unsigned*>(row));
             w[i] = L::cx(i) > 0 ? __byte_perm(__ldg(reinterpret_cast<const unsigned*>(row + (xm1 - 1))), b, 0x5432)
                                 : __byte_perm(b, __ldg(reinterpret_cast<const unsigned*>(row + xp2)), 0x5432);
         } else {
-            const unsigned short* r16 = reinterpret_cast<const unsigned short*>(row);
-            const unsigned lo = L::cx(i) > 0 ? __ldg(r16 + xm1) : __ldg(r16 + 1);  // sources x0 -+ 1
-            const unsigned hi = L::cx(i) > 0 ? __ldg(r16) : __ldg(r16 + xp2);      // sources x0, x0 + 2
+            const unsigned lo = L::cx(i) > 0 ? ld_pop<unsigned short, INPLACE>(row + xm1)
+                                             : ld_pop<unsigned short, INPLACE>(row + 1);  // sources x0 -+ 1
+            const unsigned hi = L::cx(i) > 0 ? ld_pop<unsigned short, INPLACE>(row)
+                                             : ld_pop<unsigned short, INPLACE>(row + xp2);  // sources x0, x0 + 2
             w[i] = lo | (hi << 16);
         }
     }
@@ -197,11 +209,20 @@ struct PairTraits {
     static constexpr int kLoad = FORM == FORM_SHIFT_FX ? LD_WORDS : LD_HALVES;
 };
 
-template <int Q, class S, int FORM>
+// MODE: MODE_TWO_LATTICE (pull from fin, store into fout at the cell pair),
+// MODE_AA_EVEN (in place; read the pair's own slots i, write f*_i into the
+// pair's own slot opp(i): the launcher passes fout with the planes permuted,
+// so the store is the two-lattice one) or MODE_AA_ODD (in place; read slot
+// opp(i) at x - c_i: fin with permuted planes and the pull gather; write slot i
+// at x + c_i). In the AA steps every population is read and written by the
+// same thread, so the in-place update needs no synchronisation.
+template <int Q, class S, int FORM, int MODE>
 __global__ void __launch_bounds__(256, PairTraits<FORM>::kMinBlocks)
 k_step_pair(Planes<const typename S::T, Q> fin, Planes<typename S::T, Q> fout, const float* __restrict__ varpi,
             Geometry g, Phys<float> ph, float s, float inv_s, const float* __restrict__ varpi3) {
     using P = Pair16<S>;
+    using L = Lat<Q>;
+    using T = typename S::T;
     const int xp = blockIdx.x * blockDim.x + threadIdx.x;  // pair index along x
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -213,12 +234,39 @@ k_step_pair(Planes<const typename S::T, Q> fin, Planes<typename S::T, Q> fout, c
     const int xp2 = x0 + 2 >= g.nx ? -x0 : 2;
 
     PackedPairs<S, Q> d;  // the loaded words; lane 0: cell x0, lane 1: cell x0 + 1
-    pair_gather_words<Q, S, PairTraits<FORM>::kLoad>(fin, cell, nb, xm1, xp2, d.w);
+    if constexpr (MODE == MODE_AA_EVEN) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d.w[i] = ld_pop<unsigned, true>(fin.p[i] + cell);
+    } else if constexpr (MODE == MODE_AA_ODD) {
+        pair_gather_words<Q, S, LD_HALVES, true>(fin, cell, nb, xm1, xp2, d.w);
+    } else {
+        pair_gather_words<Q, S, PairTraits<FORM>::kLoad>(fin, cell, nb, xm1, xp2, d.w);
+    }
 
-    // each post-collision pair of values is stored as one 32-bit word as soon as it is final
+    // each post-collision pair of values is stored as soon as it is final: one 32-bit word at
+    // the pair, or (odd AA step) at the pair shifted by c_i, split into two 16-bit stores when
+    // the shift is along x
     const auto store = [&](int i, F2 v) {
         const float2 f = v.split();
-        *reinterpret_cast<unsigned*>(fout.p[i] + cell) = P::pack(f.x, f.y);
+        if constexpr (MODE == MODE_AA_ODD) {
+            int o = 0;  // y/z part of the push offset
+            if (L::cy(i) > 0) o += nb.oyp;
+            if (L::cy(i) < 0) o += nb.oym;
+            if (L::cz(i) > 0) o += nb.ozp;
+            if (L::cz(i) < 0) o += nb.ozm;
+            T* row = fout.p[i] + (cell + o);
+            if (L::cx(i) == 0) {
+                *reinterpret_cast<unsigned*>(row) = P::pack(f.x, f.y);
+            } else if (L::cx(i) > 0) {  // targets x0 + 1, x0 + 2
+                S::store_raw(row, 1, f.x);
+                S::store_raw(row, xp2, f.y);
+            } else {  // targets x0 - 1, x0
+                S::store_raw(row, xm1, f.x);
+                S::store_raw(row, 0, f.y);
+            }
+        } else {
+            *reinterpret_cast<unsigned*>(fout.p[i] + cell) = P::pack(f.x, f.y);
+        }
     };
     if (FORM == FORM_ANISO) {
         float2 v3[3];
@@ -233,8 +281,10 @@ k_step_pair(Planes<const typename S::T, Q> fin, Planes<typename S::T, Q> fout, c
     }
 }
 
-// Launch of the paired kernel; the caller has checked pair_applies().
-template <int Q, class S, int FORM>
+// Launch of the paired kernel; the caller has checked pair_applies(). The AA
+// steps run in place (fin and fout are the same buffer) with the planes of
+// their gathered (odd step) or stored (even step) side permuted to opp(i).
+template <int Q, class S, int FORM, int MODE>
 cudaError_t step_pair_impl(const LaunchCtx& c, const void* fin, void* fout, const float* varpi) {
     using T = typename S::T;
     Geometry g{c.nx, c.ny, c.nz, 0, 0, 0, (size_t)c.nx * c.ny * c.nz};
@@ -246,29 +296,51 @@ cudaError_t step_pair_impl(const LaunchCtx& c, const void* fin, void* fout, cons
     Planes<const T, Q> a;
     Planes<T, Q> b;
     for (int i = 0; i < Q; ++i) {
-        a.p[i] = static_cast<const T*>(fin) + (size_t)i * g.N;
-        b.p[i] = static_cast<T*>(fout) + (size_t)i * g.N;
+        const int ia = MODE == MODE_AA_ODD ? opp<Q>(i) : i;
+        const int ib = MODE == MODE_AA_EVEN ? opp<Q>(i) : i;
+        a.p[i] = static_cast<const T*>(fin) + (size_t)ia * g.N;
+        b.p[i] = static_cast<T*>(fout) + (size_t)ib * g.N;
     }
-    k_step_pair<Q, S, FORM><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, float(c.scale), float(1.0 / c.scale),
-                                                       c.varpi3);
+    k_step_pair<Q, S, FORM, MODE><<<grd, blk, 0, c.stream>>>(a, b, varpi, g, ph, float(c.scale),
+                                                             float(1.0 / c.scale), c.varpi3);
     return cudaGetLastError();
 }
 
-// The paired kernel covers periodic two-lattice steps of lattices with an
-// even nx (aligned pair words in every plane) and 32-bit indices.
+// The paired kernel covers periodic lattices with an even nx (aligned pair
+// words in every plane) and 32-bit indices: two-lattice steps in every
+// collision form, AA steps in the equilibrium-shift forms.
 inline bool pair_applies(const LaunchCtx& c, int mode) {
-    return c.variant == 0 && mode == MODE_TWO_LATTICE && !c.wall[0] && !c.wall[1] && !c.wall[2] && !c.links &&
-           c.nx >= 2 && (c.nx % 2) == 0 && (size_t)c.q * c.nx * c.ny * c.nz < ((size_t)1 << 31);
+    if (c.variant != 0 || c.wall[0] || c.wall[1] || c.wall[2] || c.links || c.nx < 2 || (c.nx % 2) != 0 ||
+        (size_t)c.q * c.nx * c.ny * c.nz >= ((size_t)1 << 31))
+        return false;
+    if (mode == MODE_TWO_LATTICE) return true;
+    const int form = step_form(c, c.q);
+    return (mode == MODE_AA_EVEN || mode == MODE_AA_ODD) && (form == FORM_SHIFT_FX || form == FORM_SHIFT);
+}
+
+template <int Q, class S, int MODE>
+cudaError_t step_pair_forms(const LaunchCtx& c, const void* fin, void* fout, const float* varpi) {
+    if constexpr (MODE == MODE_TWO_LATTICE) {
+        switch (step_form(c, Q)) {
+            case FORM_SHIFT_FX: return step_pair_impl<Q, S, FORM_SHIFT_FX, MODE>(c, fin, fout, varpi);
+            case FORM_SHIFT: return step_pair_impl<Q, S, FORM_SHIFT, MODE>(c, fin, fout, varpi);
+            case FORM_DRAG: return step_pair_impl<Q, S, FORM_DRAG, MODE>(c, fin, fout, varpi);
+            default: return step_pair_impl<Q, S, FORM_ANISO, MODE>(c, fin, fout, varpi);
+        }
+    } else {
+        return step_form(c, Q) == FORM_SHIFT_FX ? step_pair_impl<Q, S, FORM_SHIFT_FX, MODE>(c, fin, fout, varpi)
+                                                : step_pair_impl<Q, S, FORM_SHIFT, MODE>(c, fin, fout, varpi);
+    }
 }
 
 template <int Q, class S>
-cudaError_t step_pair_forms(const LaunchCtx& c, const void* fin, void* fout, const float* varpi) {
-    switch (step_form(c, Q)) {
-        case FORM_SHIFT_FX: return step_pair_impl<Q, S, FORM_SHIFT_FX>(c, fin, fout, varpi);
-        case FORM_SHIFT: return step_pair_impl<Q, S, FORM_SHIFT>(c, fin, fout, varpi);
-        case FORM_DRAG: return step_pair_impl<Q, S, FORM_DRAG>(c, fin, fout, varpi);
-        default: return step_pair_impl<Q, S, FORM_ANISO>(c, fin, fout, varpi);
+cudaError_t step_pair_modes(const LaunchCtx& c, int mode, const void* fin, void* fout, const float* varpi) {
+    switch (mode) {
+        case MODE_TWO_LATTICE: return step_pair_forms<Q, S, MODE_TWO_LATTICE>(c, fin, fout, varpi);
+        case MODE_AA_EVEN: return step_pair_forms<Q, S, MODE_AA_EVEN>(c, fin, fout, varpi);
+        case MODE_AA_ODD: return step_pair_forms<Q, S, MODE_AA_ODD>(c, fin, fout, varpi);
     }
+    return cudaErrorInvalidValue;
 }
 
 // Step kernels of a 16-bit storage policy: the paired kernel where it
@@ -276,8 +348,8 @@ cudaError_t step_pair_forms(const LaunchCtx& c, const void* fin, void* fout, con
 template <class S>
 cudaError_t step_for_storage16(const LaunchCtx& c, int mode, const void* fin, void* fout, const float* varpi) {
     if (pair_applies(c, mode)) {
-        if (c.q == 9) return step_pair_forms<9, S>(c, fin, fout, varpi);
-        if (c.q == 19) return step_pair_forms<19, S>(c, fin, fout, varpi);
+        if (c.q == 9) return step_pair_modes<9, S>(c, mode, fin, fout, varpi);
+        if (c.q == 19) return step_pair_modes<19, S>(c, mode, fin, fout, varpi);
         return cudaErrorInvalidValue;
     }
     return step_for_storage<S>(c, mode, fin, fout, varpi);

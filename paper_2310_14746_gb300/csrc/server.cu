@@ -50,15 +50,22 @@ constexpr int kMaxSlots = 1024;
 // for the large slots that run the single-lattice kernels.
 constexpr int kDirectClass = 8;
 constexpr int kClasses = 9;
-// Slots of at least this many cells (96^3 and larger at the serving edges) run the
+// Slots of at least this many cells (64^3 and larger at the serving edges) run the
 // single-lattice step kernels, one launch per slot and step inside the round's
-// graph: such a slot fills the GPU on its own, and the tile kernel's per-block
-// slot lookup (a chain of dependent loads before the first population load)
-// costs it 10 to 15 % of the copy bandwidth (measured: 128^3 FP32 0.90 vs 0.99,
-// 192^3 FP16 0.70 vs 0.83). Smaller slots share the tile kernel, where one launch
-// per class replaces one per slot.
-constexpr size_t kDirectCells = (size_t)1 << 19;
+// graph, each slot in a branch of the graph (kGraphBranches) so that the
+// launches of several slots overlap: the tile kernel's per-block slot lookup (a
+// chain of dependent loads before the first population load) costs 10 to 15 % of
+// the copy bandwidth (measured: 128^3 FP32 0.90 vs 0.99, 192^3 FP16 0.70 vs 0.83;
+// eight 64^3 slots in parallel branches 0.80 vs 0.70 FP16, 0.98 vs 0.89 FP32).
+// Smaller slots share the tile kernel, where one launch per class replaces one
+// launch per slot.
+constexpr size_t kDirectCells = (size_t)1 << 18;
 constexpr int kBlock = 256;  // threads per block; a tile is tw x (256 / tw) threads of one slot
+// Parallel branches of a round's graph: the tile-kernel classes on one, the large
+// slots spread over the others. A slot's steps depend only on its own previous
+// step, so the branches are independent, and their kernels (and the partly
+// filled last wave of each launch) overlap on the GPU.
+constexpr int kGraphBranches = 8;
 
 struct DevSlot {
     void* f[2];
@@ -415,6 +422,8 @@ struct hlbm_server {
     std::vector<uint64_t> table_ids;  // request ids of the slots in the device table, in order
     size_t budget = 0, used = 0;
     cudaStream_t stream = nullptr, cap_stream = nullptr;
+    cudaStream_t branch[kGraphBranches] = {};  // capture streams of the graph's parallel branches
+    cudaEvent_t fork_ev = nullptr, join_ev[kGraphBranches] = {};
     int device = 0;
     std::mutex mu;
     std::deque<Pending> waiting;
@@ -612,19 +621,18 @@ cudaError_t widen_to_fp32(hlbm_server_t* s, Live& l) {
     return cudaSuccess;
 }
 
-// Capture check_every steps (per step: the reduced-precision slots' kernel, then
-// the FP32 slots' kernel) with the current grid sizes.
+// Capture check_every steps of this round's slots with the current grid sizes:
+// the tile-kernel classes (per step: the reduced-precision classes, then the
+// FP32 ones) on one branch, each large slot's single-lattice launches on one of
+// the other branches (round robin), all forked from and joined into the
+// capture stream.
 int build_graph(hlbm_server_t* s) {
     if (!s->cap_stream) SRV_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
-    cudaGraph_t graph = nullptr;
-    SRV_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t le = cudaSuccess;
-    const auto launch = [&](auto kern, int blocks, int k) {
-        if (blocks > 0 && le == cudaSuccess) {
-            kern<<<blocks, kBlock, 0, s->cap_stream>>>(s->dtab, k);
-            le = cudaGetLastError();
-        }
-    };
+    if (!s->fork_ev) SRV_CUDA(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming));
+    for (int b = 0; b < kGraphBranches; ++b) {
+        if (!s->branch[b]) SRV_CUDA(cudaStreamCreateWithFlags(&s->branch[b], cudaStreamNonBlocking));
+        if (!s->join_ev[b]) SRV_CUDA(cudaEventCreateWithFlags(&s->join_ev[b], cudaEventDisableTiming));
+    }
     s->graph_direct.clear();
     std::vector<const Live*> direct;
     for (int idx : s->run) {
@@ -634,12 +642,28 @@ int build_graph(hlbm_server_t* s) {
             s->graph_direct.emplace_back(l.p.id, l.ds.storage);
         }
     }
-    for (int k = 0; k < s->check_every; ++k) {
+    bool tiles = false;
+    for (int c = 0; c < 8; ++c) tiles = tiles || s->grid[c] > 0;
+    const int first_direct = tiles ? 1 : 0;  // branch 0 carries the tile kernels when there are any
+    const int direct_branches = kGraphBranches - first_direct;
+    const int used = std::min<int>(kGraphBranches, first_direct + (int)direct.size());
+    cudaGraph_t graph = nullptr;
+    SRV_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaEventRecord(s->fork_ev, s->cap_stream);
+    for (int b = 0; b < used && le == cudaSuccess; ++b) le = cudaStreamWaitEvent(s->branch[b], s->fork_ev, 0);
+    const auto launch = [&](auto kern, int blocks, int k) {
+        if (blocks > 0 && le == cudaSuccess) {
+            kern<<<blocks, kBlock, 0, s->branch[0]>>>(s->dtab, k);
+            le = cudaGetLastError();
+        }
+    };
+    for (int k = 0; k < s->check_every && le == cudaSuccess; ++k) {
         const int* g = s->grid;
-        for (const Live* l : direct) {  // launch k reads f[k & 1], writes f[(k + 1) & 1]
+        for (size_t d = 0; d < direct.size(); ++d) {  // launch k reads f[k & 1], writes f[(k + 1) & 1]
             if (le != cudaSuccess) break;
+            const Live* l = direct[d];
             LaunchCtx c = s->ctx_for(*l);
-            c.stream = s->cap_stream;
+            c.stream = s->branch[first_direct + (int)(d % direct_branches)];
             le = launch_step(c, MODE_TWO_LATTICE, l->ds.f[k & 1], l->ds.f[(k + 1) & 1], l->ds.varpi);
         }
         launch(k_batched_step<StoreF16, true>, g[2 * HLBM_F16DEV + 1], k);
@@ -648,6 +672,10 @@ int build_graph(hlbm_server_t* s) {
         launch(k_batched_step<StoreBF16, false>, g[2 * HLBM_BF16DEV], k);
         launch(k_batched_step<StoreF32, true>, g[2 * HLBM_F32 + 1], k);
         launch(k_batched_step<StoreF32, false>, g[2 * HLBM_F32], k);
+    }
+    for (int b = 0; b < used && le == cudaSuccess; ++b) {
+        le = cudaEventRecord(s->join_ev[b], s->branch[b]);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(s->cap_stream, s->join_ev[b], 0);
     }
     cudaError_t e = cudaStreamEndCapture(s->cap_stream, &graph);
     if (e == cudaSuccess && le != cudaSuccess) {
@@ -832,6 +860,11 @@ void hlbm_server_destroy(hlbm_server_t* s) {
     cudaStreamSynchronize(s->stream);
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    for (int b = 0; b < kGraphBranches; ++b) {
+        if (s->branch[b]) cudaStreamDestroy(s->branch[b]);
+        if (s->join_ev[b]) cudaEventDestroy(s->join_ev[b]);
+    }
+    if (s->fork_ev) cudaEventDestroy(s->fork_ev);
     cudaFree(s->dtab);
     cudaFree(s->dout);
     cudaFree(s->dfeq);

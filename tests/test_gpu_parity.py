@@ -134,17 +134,20 @@ def test_patterns_bitwise_identical_fp32():
         np.testing.assert_array_equal(a.get_populations(), b.get_populations())
 
 
-@pytest.mark.parametrize("storage", [hb.HLBM_F32, hb.HLBM_F16DEV])
+@pytest.mark.parametrize("storage", [hb.HLBM_F32, hb.HLBM_F16DEV, hb.HLBM_BF16DEV])
+@pytest.mark.parametrize("fx_only", [False, True])
 @pytest.mark.parametrize("q,shape", [(19, (3, 4, 5)), (19, (4, 5, 45)), (19, (2, 3, 130)), (19, (3, 2, 256)),
-                                     (19, (2, 5, 200)), (9, (1, 7, 131)), (9, (1, 3, 64))])
-def test_aa_periodic_bitwise(q, shape, storage):
-    """Fully periodic lattices in FP32 and FP16 storage (the in-place kernels without wall
-    logic): rows narrower than a warp, one and several 128-cell row segments, ragged last
-    segments. The AA state equals the two-lattice state bit for bit after odd and even step
-    counts."""
+                                     (19, (2, 5, 200)), (19, (3, 3, 2)), (19, (4, 3, 64)), (9, (1, 7, 131)),
+                                     (9, (1, 3, 64))])
+def test_aa_periodic_bitwise(q, shape, storage, fx_only):
+    """Fully periodic lattices (the in-place kernels without wall logic; for 16-bit storage and
+    an even nx the paired two-cells-per-thread AA kernels, in both equilibrium-shift forms):
+    rows narrower than a warp, one and several 128-cell row segments, ragged last segments, a
+    row of a single cell pair. The AA state equals the two-lattice state of the per-cell kernel
+    bit for bit after odd and even step counts."""
     vp = inputs.random_porosity(shape, seed=18, lo=0.2)
     f0 = inputs.random_populations(q, shape, seed=19, amplitude=0.2)
-    F = (1e-5, 2e-6, -3e-6 if q == 19 else 0.0)
+    F = (1e-5, 0.0, 0.0) if fx_only else (1e-5, 2e-6, -3e-6 if q == 19 else 0.0)
     a = make_lattice(q, shape, storage, hb.HLBM_TWO_LATTICE, 0.6, F, (0, 0, 0), varpi=vp, f0=f0)
     b = make_lattice(q, shape, storage, hb.HLBM_AA, 0.6, F, (0, 0, 0), varpi=vp, f0=f0)
     a.set_step_kernel(hb.HLBM_STEP_PER_CELL)  # the same per-cell arithmetic as the AA kernels

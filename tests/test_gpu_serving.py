@@ -54,13 +54,15 @@ def test_server_fp32_matches_single_lattice_and_oracle(oracle):
 def test_same_result_alone_and_in_mix(storage):
     """Each request's result (steps, permeability, residual, velocity field) is bit-identical
     when it runs alone and when it shares the batch with requests of other sizes that
-    arrive, run and retire around it."""
+    arrive, run and retire around it. The 96^3 request runs on the single-lattice kernels in a
+    branch of the round's graph of its own, beside the tile kernels of the small ones."""
     fa = field(32, 16, 0.35)
     fb = field(64, 32, 0.2)
     fc = field((48, 40, 24), 8, 0.3)
+    fd = field(96, 32, 0.25)
     kw = dict(tau=0.6, F=(1e-5, 0, 0), tol=1e-7, max_steps=3000, want_u=True)
     alone = {}
-    for name, f in (("a", fa), ("b", fb), ("c", fc)):
+    for name, f in (("a", fa), ("b", fb), ("c", fc), ("d", fd)):
         srv = Server(1 << 30, storage, 100)
         srv.submit(f, tag=ord(name), **kw)
         (r,) = srv.run_until_idle()
@@ -71,6 +73,7 @@ def test_same_result_alone_and_in_mix(storage):
     srv.pump()
     srv.pump()
     srv.submit(fa, tag=ord("a"), **kw)
+    srv.submit(fd, tag=ord("d"), **kw)
     srv.pump()
     srv.submit(fc, tag=ord("c"), **kw)
     mixed = {r["tag"]: r for r in srv.run_until_idle()}
