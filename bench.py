@@ -49,6 +49,9 @@ KERNEL_TRAFFIC_BYTES = {
     # k_step<19, StoreF32, periodic, two-lattice, int, shift-fx>, 256^3: mean of two launches
     # (1342250752 + 1228698112 and 1342237696 + 1217931008 bytes)
     ("stream_collide_d3q19_f32_two", 256): {"bytes": 2565558784, "source_hash": "76d4a47919d1105a"},
+    # k_step<19, StoreF32, periodic, AA even / AA odd, int, shift-fx>, 256^3: mean of the even
+    # (1342202368 + 1217577984) and odd (1342190336 + 1217456640 bytes) launch of one capture
+    ("stream_collide_d3q19_f32_aa", 256): {"bytes": 2559713664, "source_hash": "76d4a47919d1105a"},
     # k_step_pair<19, StoreF16, shift-fx, two-lattice>, 384^3 Boolean sphere matrix: mean of two launches
     # (2378683648 + 2107668736 and 2378212864 + 2106361088 bytes)
     ("stream_collide_d3q19_f16_two", 384): {"bytes": 4485463168, "source_hash": "4c5af8f94e7e5453"},
