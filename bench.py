@@ -16,6 +16,13 @@ roofline : the stream-collide kernel's algorithmic bytes (q*2*sizeof(T) + 4 per 
 cpu_baseline : the FP64 CPU oracle timed on the host cores on a bounded sample (a few
         time steps of the same 256^3 workload).
 
+Legs of the default line: "aa" (the workload in place), "reduced_precision" (FP16 / BF16 at
+384^3 on the random sphere matrix, and their error against the FP64 oracle at 96^3),
+"adjoint" (the 128^3 x 2000-step gradient), "serving" (16 requests of the serving trace,
+batched server vs the plain FP32 loop, with the served results against FP64).
+Other modes: --workload W (another lattice workload), --serving-only (a longer serving trace),
+--serving-class (throughput of server slot sets), --adjoint-only.
+
 --impl reference times that oracle alone (the deliberately slow reference program) on
 the same workload and prints the same line with "impl": "reference".
 Multi-GPU (torchrun): independent replicas, one lattice per GPU (weak scaling); the
