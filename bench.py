@@ -60,14 +60,14 @@ KERNEL_TRAFFIC_BYTES = {
     # (1342202368 + 1217577984) and odd (1342190336 + 1217456640 bytes) launch of one capture
     ("stream_collide_d3q19_f32_aa", 256): {"bytes": 2559713664, "source_hash": "76d4a47919d1105a"},
     # k_step_pair<19, StoreF16, shift-fx, two-lattice>, 384^3 Boolean sphere matrix: mean of two launches
-    # (2378683648 + 2107668736 and 2378212864 + 2106361088 bytes)
-    ("stream_collide_d3q19_f16_two", 384): {"bytes": 4485463168, "source_hash": "4c5af8f94e7e5453"},
-    # k_step_pair<19, StoreBF16, shift-fx, two-lattice>, 384^3 Boolean sphere matrix: mean of two launches
-    # (2378648064 + 2109742336 and 2378214912 + 2107992064 bytes)
-    ("stream_collide_d3q19_bf16_two", 384): {"bytes": 4487298688, "source_hash": "7aa28bbe2bf10de0"},
-    # k_step_pair<19, StoreF16, shift-fx, AA even / AA odd>, 384^3 Boolean sphere matrix: mean of the
-    # even (2378228736 + 2098037760) and odd (2378235392 + 2152788992 bytes) launch of one capture
-    ("stream_collide_d3q19_f16_aa", 384): {"bytes": 4503645440, "source_hash": "4c5af8f94e7e5453"},
+    # (2378278656 + 2107357184 and 2378211072 + 2106170112 bytes)
+    ("stream_collide_d3q19_f16_two", 384): {"bytes": 4485008512, "source_hash": "59ee95aa12972e25"},
+    # k_step_pair<19, StoreBF16, shift-fx, two-lattice> (56 registers), 384^3 Boolean sphere matrix: mean of
+    # two launches (2378226176 + 2104031232 and 2378216704 + 2103352064 bytes)
+    ("stream_collide_d3q19_bf16_two", 384): {"bytes": 4481913088, "source_hash": "e6debcdf9dc15415"},
+    # k_step_pair<19, StoreF16, shift-fx, AA even / AA odd>, 384^3 Boolean sphere matrix: mean of an
+    # even (2378207744 + 2097896192) and an odd (2378275584 + 2150258944 bytes) launch
+    ("stream_collide_d3q19_f16_aa", 384): {"bytes": 4502319232, "source_hash": "59ee95aa12972e25"},
 }
 
 # the sources each step kernel is compiled from (csrc/)

@@ -216,8 +216,22 @@ struct PairTraits {
 // opp(i) at x - c_i: fin with permuted planes and the pull gather; write slot i
 // at x + c_i). In the AA steps every population is read and written by the
 // same thread, so the in-place update needs no synchronisation.
+// Block size and register budget of a paired kernel. The BF16 two-lattice
+// force-along-x kernel runs at 56 registers in 128-thread blocks (9 blocks, 36
+// resident warps per SM; measured at 384^3: 0.973 vs 0.955 of the copy
+// bandwidth at 64 registers). The FP16 kernel (whose unpack costs more
+// registers) and the in-place steps measured slower at 56 (FP16 0.919 vs 0.922,
+// AA 0.855 / 0.892 vs 0.884 / 0.912), so they keep 256-thread blocks and the
+// budget of PairTraits.
+template <class S, int FORM, int MODE>
+struct PairLaunch {
+    static constexpr bool k56 = S::kind == 3 /* BF16 */ && FORM == FORM_SHIFT_FX && MODE == MODE_TWO_LATTICE;
+    static constexpr int kThreads = k56 ? 128 : 256;
+    static constexpr int kMinBlocks = k56 ? 9 : PairTraits<FORM>::kMinBlocks;
+};
+
 template <int Q, class S, int FORM, int MODE>
-__global__ void __launch_bounds__(256, PairTraits<FORM>::kMinBlocks)
+__global__ void __launch_bounds__(PairLaunch<S, FORM, MODE>::kThreads, PairLaunch<S, FORM, MODE>::kMinBlocks)
 k_step_pair(Planes<const typename S::T, Q> fin, Planes<typename S::T, Q> fout, const float* __restrict__ varpi,
             Geometry g, Phys<float> ph, float s, float inv_s, const float* __restrict__ varpi3) {
     using P = Pair16<S>;
@@ -289,8 +303,9 @@ cudaError_t step_pair_impl(const LaunchCtx& c, const void* fin, void* fout, cons
     using T = typename S::T;
     Geometry g{c.nx, c.ny, c.nz, 0, 0, 0, (size_t)c.nx * c.ny * c.nz};
     const Phys<float> ph = make_phys<float, Q>(c.tau, c.F);
+    constexpr int threads = PairLaunch<S, FORM, MODE>::kThreads;
     const int bx = pair_block_x(c.nx);
-    const int by = bx >= 256 ? 1 : 256 / bx;
+    const int by = bx >= threads ? 1 : threads / bx;
     const dim3 blk(bx, by, 1);
     const dim3 grd((c.nx / 2 + bx - 1) / bx, (c.ny + by - 1) / by, c.nz);
     Planes<const T, Q> a;
