@@ -124,7 +124,7 @@ struct DeviceGuard {
 // I/O), stream-ordered on the handle's stream, from a memory pool private to the handle that
 // keeps what it has mapped for the next call. With the default pool (release threshold 0) the
 // 14.5 GB of checkpoints of a 128^3 x 2000-step gradient were unmapped at every
-// synchronisation and mapped again by the next call, about 15 % of the call's time.
+// synchronisation and mapped again by the next call (0.395 s vs 0.370 s per gradient).
 // hlbm_release_scratch hands the memory back; hlbm_destroy destroys the pool.
 cudaError_t scratch_alloc(hlbm_t* h, void** p, size_t bytes) {
     if (!h->pool) {

@@ -3,12 +3,14 @@
 //
 // Each admitted request owns a slot: two population buffers (two-lattice
 // streaming), its porosity field, and its residual reference velocity. A
-// device slot table lists the slots of the current round with their tile
+// device slot table lists the small slots of the current round with their tile
 // ranges, grouped by kernel class (storage and collision form); one launch
 // per class advances every listed slot by one time step, one block per tile
-// (a tile never mixes slots). check_every launches are captured once in a
-// CUDA graph that reads the table from device memory, so admissions,
-// retirements, precision changes and the round's slot set only rewrite the
+// (a tile never mixes slots). Large slots (kDirectCells) run the single-lattice
+// step kernels instead. check_every steps are captured once in a CUDA graph of
+// parallel branches (the tile kernels on one, each large slot on one of the
+// others) that reads the table from device memory, so admissions, retirements,
+// precision changes and the round's set of small slots only rewrite the
 // table. After each graph replay a per-slot FP64 reduction (a fixed partition
 // per slot, so a slot's result does not depend on its neighbours in the
 // batch) gives the residual and the apparent permeability; converged slots
