@@ -527,7 +527,7 @@ def served_vs_fp64(trace, res_b, res_p, field_of, max_edge=64, lu_budget=1.2e10,
 
 
 def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, world=1, dist=None,
-                capacity_requests=0):
+                capacity_requests=0, backfill=None):
     """Serving stream sample: the first n_requests of the seeded trace (edges up to max_edge).
     1) capacity: all requests (or the first capacity_requests of them) at t = 0 through the
        batched FP16 server -> solves/s;
@@ -553,7 +553,7 @@ def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, 
         field_of(rq)
     cap_set = base[:capacity_requests] if capacity_requests > 0 else base
     res0, info0 = sv.run_stream(cap_set, field_of, storage=hb.HLBM_F16DEV, mem_budget=budget_gb << 30, tol=tol,
-                                realtime=False)
+                                realtime=False, backfill=backfill)
     cap = len(res0) / max(max(r["t_finish"] for r in res0), 1e-9)
     rate = 0.8 * cap
     trace = [dict(rq) for rq in base]
@@ -564,7 +564,7 @@ def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, 
         rq["arrival_s"] = t
     want_u = len(trace) <= 64  # final velocities kept on the host for the comparison
     res_b, info_b = sv.run_stream(trace, field_of, storage=hb.HLBM_F16DEV, mem_budget=budget_gb << 30, tol=tol,
-                                  want_u=want_u)
+                                  want_u=want_u, backfill=backfill)
     res_p, info_p = sv.plain_loop(trace, field_of, tol=tol, want_u=want_u)
     kb = {r["tag"]: r["k_app"] for r in res_b}
     kp = {r["tag"]: r["k_app"] for r in res_p}
@@ -601,6 +601,7 @@ def serving_leg(n_requests, seed, max_edge=192, tol=1e-6, budget_gb=64, rank=0, 
         by_edge[str(e)] = {"n": len(tb), "batched": sv.percentiles(tb), "plain": sv.percentiles(tp)}
     return {
         "requests": len(trace), "edges": sorted({r["edge"] for r in trace}), "tol_max_du": tol,
+        "backfill": backfill if backfill is not None else "library default",
         "capacity_solves_per_s": cap, "capacity_requests": len(cap_set), "arrival_rate_per_s": rate,
         "by_edge": by_edge if len(trace) > 32 else None,
         "lattice_updates": {"batched": int(lu_all), "low_precision": int(lu_low)},
@@ -702,7 +703,8 @@ def run_serving_only(args, rank, world, local_rank):
     build.build()
     t0 = time.perf_counter()
     serving = serving_leg(args.serving_requests, 2310147460 + 4, max_edge=args.serving_max_edge,
-                          rank=rank, world=world, capacity_requests=args.serving_capacity_requests)
+                          rank=rank, world=world, capacity_requests=args.serving_capacity_requests,
+                          backfill=args.serving_backfill)
     if rank == 0:
         print(json.dumps({"metric": METRIC, "impl": "ours", "mode": "serving-only", "n_gpus": world,
                           "wall_s": time.perf_counter() - t0, "serving": serving}), flush=True)
@@ -863,6 +865,8 @@ def main():
     ap.add_argument("--serving-max-edge", type=int, default=128)
     ap.add_argument("--serving-capacity-requests", type=int, default=0,
                     help="measure the batched capacity on the first K requests only (0: all of them)")
+    ap.add_argument("--serving-backfill", type=float, default=None,
+                    help="age-priority window of the batched server in the serving leg (default: the library's)")
     ap.add_argument("--serving-only", action="store_true",
                     help="run only the serving leg (long traces) and print its JSON object")
     ap.add_argument("--serving-class", default="",
