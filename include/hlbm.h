@@ -196,10 +196,11 @@ int hlbm_set_homogenization(hlbm_t* h, int form);
 /* Which of the equivalent step kernels runs (no counterpart in the paper: an
  * implementation choice, exposed for testing and measurement).
  * HLBM_STEP_AUTO (default) picks the fastest kernel that applies: for FP16
- * and BF16 storage on periodic two-lattice lattices with an even nx, a
- * kernel that updates two neighbouring cells per thread with 32-bit words.
- * HLBM_STEP_PER_CELL forces the one-cell-per-thread kernel. Both give
- * bit-identical states. */
+ * and BF16 storage on periodic lattices with an even nx, a kernel that
+ * updates two neighbouring cells per thread with 32-bit words (two-lattice
+ * streaming in every homogenization form; in-place AA streaming in the
+ * equilibrium-shift form with a scalar varpi field). HLBM_STEP_PER_CELL forces
+ * the one-cell-per-thread kernel. Both give bit-identical states. */
 #define HLBM_STEP_AUTO 0
 #define HLBM_STEP_PER_CELL 1
 int hlbm_set_step_kernel(hlbm_t* h, int variant);
